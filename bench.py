@@ -1,0 +1,321 @@
+#!/usr/bin/env python
+"""Benchmark of the explicit ARK step on GB300.
+
+Workload (default): 3D Rayleigh-Benard layer, 512 x 512 x 256 cells, box
+2 x 2 x 1, polytrope m = 0.1, chi = 1.1, Ra = 1e7, Pr = 1, no-slip
+fixed-temperature walls in z, periodic in x and y, velocity perturbation
+U(-1e-3, 1e-3) from numpy default_rng(4) -- synthetic data built by
+``paper_1903_09043_gb300.inputs``.  A step is one launch of the fused step
+kernel over all 64 Mi cells (acoustic faces, tilde states, transport,
+viscous and heat fluxes, next CFL time step).
+
+Paths timed: ``f32split`` (headline: FP32 state and stencil arithmetic, FP64
+base state) and ``f64`` (FP64 throughout).  ``--impl reference`` times the
+FP64 CPU oracle on slabs of the same workload instead.
+
+Output: one JSON line on rank 0.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import math
+import os
+import statistics
+import subprocess
+import sys
+import tempfile
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+if ROOT not in sys.path:
+    sys.path.insert(0, ROOT)
+
+METRIC = "cell-updates/s per time step"
+UNIT = "cell-updates/s"
+WORKLOAD = {"workload": "rayleigh_benard_3d_512x512x256", "dim": 3, "n": [512, 512, 256], "box": [2.0, 2.0, 1.0],
+            "polytrope_m": 0.1, "chi": 1.1, "Ra": 1e7, "Pr": 1.0, "perturbation": 1e-3, "seed": 4,
+            "bc": "periodic x,y; no-slip fixed-T walls z", "low_mach": 1, "cfl": 0.8}
+# algorithmic HBM bytes per cell-update: every conserved field read once and written once
+ALG_BYTES = {("f64", 3): 80, ("f32", 3): 40, ("f32split", 3): 40, ("f64", 2): 64, ("f32", 2): 32, ("f32split", 2): 32}
+STEP_KERNEL = "ark_step_kernel"
+
+
+def make_workload():
+    from paper_1903_09043_gb300 import inputs as I
+    w = WORKLOAD
+    return I.rayleigh_benard(3, tuple(w["n"]), m=w["polytrope_m"], chi=w["chi"], Ra=w["Ra"], Pr=w["Pr"],
+                             amp=w["perturbation"], seed=w["seed"], low_mach=w["low_mach"], cfl=w["cfl"])
+
+
+def measured_peaks():
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            return json.load(f), "measured"
+    except Exception:
+        return {"hbm_gbs": 6800.0, "bf16_tflops": 1900.0}, "fallback"
+
+
+def kernel_traffic(path):
+    """DRAM bytes per launch of the step kernel from a committed ncu summary,
+    valid only while the kernel source is unchanged (hash recorded with it)."""
+    import hashlib
+    try:
+        with open(os.path.join(ROOT, "profiles", "step_kernel_traffic.json")) as f:
+            rec = json.load(f)
+        h = hashlib.sha256()
+        for name in ("ark_step.cuh", "ark_common.cuh"):
+            with open(os.path.join(ROOT, "paper_1903_09043_gb300", "csrc", name), "rb") as g:
+                h.update(g.read())
+        if rec.get("source_sha256") != h.hexdigest():
+            return None
+        ent = rec.get("paths", {}).get(path)
+        return ent.get("bytes_per_launch_full") if ent else None
+    except Exception:
+        return None
+
+
+class ClockSampler:
+    """nvidia-smi clocks and throttle reasons sampled every 50 ms."""
+
+    FIELDS = ["clocks.sm", "clocks.max.sm", "power.draw", "clocks_event_reasons.hw_slowdown",
+              "clocks_event_reasons.hw_thermal_slowdown", "clocks_event_reasons.sw_thermal_slowdown",
+              "clocks_event_reasons.sw_power_cap"]
+
+    def __init__(self, index: int):
+        self.index = index
+        self.proc = None
+        self.file = None
+
+    def start(self):
+        try:
+            self.file = tempfile.NamedTemporaryFile(mode="w+", suffix=".csv", delete=False)
+            self.proc = subprocess.Popen(["nvidia-smi", "-i", str(self.index), "--query-gpu=" + ",".join(self.FIELDS),
+                                          "--format=csv,noheader,nounits", "-lms", "50"], stdout=self.file,
+                                         stderr=subprocess.DEVNULL)
+        except Exception:
+            self.proc = None
+
+    def stop(self):
+        if not self.proc:
+            return None
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except Exception:
+            self.proc.kill()
+        self.file.flush()
+        self.file.seek(0)
+        rows = [r.strip().split(", ") for r in self.file.read().splitlines() if r.strip()]
+        os.unlink(self.file.name)
+        sm, smax, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for r in rows:
+            if len(r) < 7:
+                continue
+            try:
+                sm.append(float(r[0]))
+                smax.append(float(r[1]))
+            except ValueError:
+                continue
+            for k, v in zip(names, r[3:7]):
+                if v.strip().lower() == "active":
+                    reasons.add(k)
+        if not sm:
+            return None
+        return {"sm_mhz": statistics.median(sm), "sm_max_mhz": max(smax), "reasons": sorted(reasons),
+                "samples": len(sm)}
+
+
+def dist_setup():
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return world, rank, local
+
+
+def barrier_and_max(value, world):
+    if world <= 1:
+        return value
+    import torch
+    import torch.distributed as dist
+    t = torch.tensor([value], dtype=torch.float64, device="cuda")
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def cpu_baseline(prob, U, seconds=10.0):
+    """The FP64 oracle on one-step slabs of the workload (8 z planes each)."""
+    import oracle as O
+    cores = os.cpu_count() or 1
+    O.set_threads(cores)
+    dt = O.dt(prob, U)
+    nz = prob.n[2]
+    cells = 0
+    t0 = time.perf_counter()
+    k = 0
+    while time.perf_counter() - t0 < seconds:
+        z0 = (8 * k) % (nz - 8)
+        O.step_window(prob, U, dt, [0, 0, z0], [prob.n[0], prob.n[1], z0 + 8])
+        cells += prob.n[0] * prob.n[1] * 8
+        k += 1
+    el = time.perf_counter() - t0
+    return {"value": cells / el, "unit": UNIT, "cores": cores, "kind": "oracle",
+            "sample": f"{k} one-step slabs of 512x512x8 cells of the workload (FP64 oracle, OpenMP {cores} threads)"}
+
+
+def run_reference(args, world, rank):
+    if rank != 0:
+        return
+    import oracle as O
+    prob, U = make_workload()
+    cores = os.cpu_count() or 1
+    O.set_threads(cores)
+    dt = O.dt(prob, U)
+    nz = prob.n[2]
+    slab = 2
+    cells = prob.n[0] * prob.n[1] * slab
+
+    def one(k):
+        z0 = (slab * k) % (nz - slab)
+        O.step_window(prob, U, dt, [0, 0, z0], [prob.n[0], prob.n[1], z0 + slab])
+
+    for k in range(args.warmup):
+        one(k)
+    t0 = time.perf_counter()
+    for k in range(args.steps):
+        one(k)
+    el = time.perf_counter() - t0
+    value = cells * args.steps / el
+    sample = f"each step: one FP64 oracle step of a 512x512x{slab} slab of the workload ({cells} cells)"
+    line = {"impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": args.gpus,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * el / args.steps,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "config": dict(WORKLOAD),
+            "cpu_baseline": {"value": value, "unit": UNIT, "cores": cores, "kind": "oracle", "sample": sample},
+            "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+
+
+def time_path(prob, U, path, args, world, stream, sampler=None):
+    import torch
+    from paper_1903_09043_gb300 import ark
+    s = ark.Solver(prob, path, stream=stream.cuda_stream)
+    s.set_state(U)
+    s.step(args.warmup)
+    torch.cuda.synchronize()
+    if world > 1:
+        import torch.distributed as dist
+        dist.barrier()
+    ev0 = torch.cuda.Event(enable_timing=True)
+    ev1 = torch.cuda.Event(enable_timing=True)
+    if sampler:
+        sampler.start()
+    torch.cuda.synchronize()
+    ev0.record(stream)
+    s.step(args.steps)
+    ev1.record(stream)
+    torch.cuda.synchronize()
+    clocks = sampler.stop() if sampler else None
+    ms = ev0.elapsed_time(ev1) / args.steps
+    ms_max = barrier_and_max(ms, world)
+    d = s.diagnostics(check=False)
+    shape = s.launch_shape()
+    s.close()
+    return ms, ms_max, d, shape, clocks
+
+
+def e2e_path(prob, U, path, args, stream):
+    """Through the C ABI with host buffers: upload the FP64 state from pinned
+    host memory, K steps each followed by a read of (t, dt), download the state."""
+    import numpy as np
+    import torch
+    from paper_1903_09043_gb300 import ark
+    pinned = torch.empty(U.shape, dtype=torch.float64, pin_memory=True)
+    host = pinned.numpy()
+    host[...] = U
+    out = torch.empty(U.shape, dtype=torch.float64, pin_memory=True).numpy()
+    s = ark.Solver(prob, path, stream=stream.cuda_stream)
+    s.set_state(host)
+    s.step(args.warmup)
+    s.time()
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    s.set_state(host)
+    for _ in range(args.steps):
+        s.step(1)
+        s.time()
+    s.get_state(out)
+    el = time.perf_counter() - t0
+    s.close()
+    nbytes = U.nbytes
+    return {"value": prob.ncells * args.steps / el, "unit": UNIT,
+            "h2d_bytes_per_step": nbytes / args.steps, "d2h_bytes_per_step": 16 + nbytes / args.steps}
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=200)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--paths", default="f32split,f64")
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-e2e", action="store_true")
+    args = ap.parse_args()
+    world, rank, local = dist_setup()
+    if args.impl == "reference":
+        run_reference(args, world, rank)
+        return
+    import torch
+    if world > 1:
+        import torch.distributed as dist
+        torch.cuda.set_device(local)
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+    else:
+        torch.cuda.set_device(0)
+    from paper_1903_09043_gb300 import ark  # noqa: F401  (fails loudly without libark.so)
+    prob, U = make_workload()
+    stream = torch.cuda.Stream()
+    peaks, peak_kind = measured_peaks()
+    hbm = float(peaks.get("hbm_gbs", 6800.0))
+    paths = [p for p in args.paths.split(",") if p]
+    results = {}
+    head = paths[0]
+    for path in paths:
+        with torch.cuda.stream(stream):
+            sampler = ClockSampler(local) if (rank == 0 and path == head) else None
+            ms, ms_max, d, shape, clocks = time_path(prob, U, path, args, world, stream, sampler)
+        cells = prob.ncells
+        B = ALG_BYTES[(path, 3)]
+        achieved = cells * B / (ms * 1e-3) / 1e9
+        traffic = kernel_traffic(path)
+        results[path] = {
+            "value": cells * world / (ms_max * 1e-3), "ms_per_step": ms_max, "dtype": "f64" if path == "f64" else "f32",
+            "roofline": {"bound": "hbm", "achieved": achieved, "peak": hbm, "unit": "GB/s", "frac": achieved / hbm,
+                         "traffic": traffic, "alg_bytes_per_cell": B, "peak_kind": f"{peak_kind} hbm_gbs (burst copy)"},
+            "launch": shape, "final_t": d["t"], "final_dt": d["dt"], "status": d["status"], "clocks": clocks,
+        }
+    h = results[head]
+    line = {"metric": METRIC, "value": h["value"], "unit": UNIT, "n_gpus": world, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": h["ms_per_step"], "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": h["dtype"], "data": "synthetic",
+            "config": dict(WORKLOAD, path=head, l2="inputs (1.3-2.7 GB) exceed L2 (129 MB); no flush",
+                           parallelism="replicas" if world > 1 else "single GPU"),
+            "roofline": h["roofline"], "clocks": h["clocks"], "gpu_launches": args.steps,
+            "paths": {p: {k: v for k, v in r.items() if k != "clocks"} for p, r in results.items()}}
+    if rank == 0 and not args.no_e2e:
+        with torch.cuda.stream(stream):
+            line["e2e"] = e2e_path(prob, U, head, args, stream)
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        line["cpu_baseline"] = cpu_baseline(prob, U)
+    if world > 1:
+        import torch.distributed as dist
+        dist.barrier()
+        dist.destroy_process_group()
+    if rank == 0:
+        print(json.dumps(line), flush=True)
+
+
+if __name__ == "__main__":
+    main()

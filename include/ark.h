@@ -1,0 +1,191 @@
+/*
+ * ark.h -- C ABI of the GB300 (sm_103a) explicit step of the all-regime,
+ * well-balanced acoustic-transport finite-volume scheme for the stratified
+ * compressible Navier-Stokes equations (Padioleau, Tremblin, Audit, Kestener,
+ * Kokh, arXiv:1903.09043).
+ *
+ * One call of ark_step advances the cell averages U = (rho, rho u, rho v
+ * [, rho w], rho*calE) by one time step of the scheme of Sec. 2:
+ *   - acoustic step with the well-balanced gravity source (Sec. 2.1.2):
+ *     per face a, S_{i+1/2}, u*, Pi*, with the low-Mach correction theta of
+ *     Eq. 16 (Sec. 2.1.5); per cell L~ and the tilde states;
+ *   - transport step, upwind on u* (Sec. 2.1.3);
+ *   - relaxation step Psi^{n+1} = Phi (Sec. 2.1.4; no change to the state);
+ *   - first-order viscous and heat-conduction fluxes (Sec. 2.2);
+ *   - the CFL time step of the next step, reduced on the device.
+ * rho*calE = rho e + rho |u|^2 / 2 + rho Phi is the total energy including the
+ * gravitational energy (Eq. 6, conservation_of_energy); the gas is ideal,
+ * p = (gamma - 1) rho e, p = rho T (Sec. 4).
+ *
+ * Conventions for every call:
+ *   - Arrays are structure-of-arrays: field f of cell (i, j[, k]) is at
+ *     U[f * N + i + nx * (j + ny * k)], N = nx * ny [* nz], x fastest, FP64.
+ *     Field order: rho, m_x, m_y, [m_z,] rho*calE (nf = dim + 2 fields).
+ *   - All device work is enqueued on the CUDA stream given to ark_create
+ *     (NULL = the legacy default stream).  Calls that return host data
+ *     synchronise that stream; ark_step does not.
+ *   - Every call returns an ark_status; nothing aborts or traps.  The text
+ *     of the last error of a handle is returned by ark_last_error.
+ *   - Handles are not thread-safe: one host thread at a time per handle.
+ */
+#ifndef ARK_H
+#define ARK_H
+
+#include <stddef.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum {
+    ARK_OK = 0,
+    ARK_ERR_INVALID_ARG = 1,   /* a parameter or pointer is out of its domain       */
+    ARK_ERR_CUDA = 2,          /* a CUDA runtime call failed (see ark_last_error)    */
+    ARK_ERR_NONPHYSICAL = 3,   /* the device saw rho <= 0, p <= 0, L~ <= 0 or a NaN  */
+    ARK_ERR_TIMEOUT = 4,       /* a bounded wait on the device ran out               */
+    ARK_ERR_UNSUPPORTED = 5,   /* valid input that this build does not implement     */
+    ARK_ERR_ALLOC = 6          /* device or host allocation failed                   */
+} ark_status;
+
+/* Boundary conditions per face of the box (ghost cells, Sec. 3.2). */
+enum {
+    ARK_BC_PERIODIC = 0,       /* wrap-around                                        */
+    ARK_BC_REFLECT_HYDRO = 1,  /* reflective wall: normal velocity mirrored with sign
+                                  flip, temperature mirrored, pressure and density
+                                  extrapolated by the discrete hydrostatic balance of
+                                  Eq. 18 (Sec. 4.3: "extrapolation of the hydrostatic
+                                  balance ... reflexive conditions for the velocity") */
+    ARK_BC_NOSLIP_FIXED_T = 2, /* no-slip wall (all velocity components mirrored with
+                                  sign flip) at a fixed temperature T_wall: ghost
+                                  T = 2 T_wall - T_mirror; p, rho as above (Sec. 4.5) */
+    ARK_BC_OUTFLOW = 3         /* zero-gradient copy of (rho, u, p)                  */
+};
+
+/* Arithmetic of the device state. */
+enum {
+    ARK_F64 = 0,               /* FP64 state and arithmetic                           */
+    ARK_F32 = 1,               /* FP32 state and arithmetic                           */
+    ARK_F32_SPLIT = 2          /* FP32 deviations from an FP64 hydrostatic base state
+                                  (per row along the gravity axis); the base-state
+                                  pressure jump minus the gravity source, and every
+                                  base-state quantity, are formed in FP64             */
+};
+
+typedef struct {
+    int dim;                   /* 2 or 3                                              */
+    int n[3];                  /* cells along x, y, z; n[2] is ignored when dim == 2  */
+    double lo[3], hi[3];       /* box corners                                         */
+} ark_grid;
+
+typedef struct {
+    double gamma;              /* adiabatic index of the ideal gas, > 1               */
+} ark_eos;
+
+typedef struct {
+    double g;                  /* uniform gravity along the LAST axis (y in 2D, z in
+                                  3D): Phi = -g * x_last at cell centres; g < 0 pulls
+                                  toward the low side.  Phi is time independent.       */
+} ark_gravity;
+
+typedef struct {
+    int lo[3], hi[3];          /* ARK_BC_* per axis and side                          */
+    double T_lo[3], T_hi[3];   /* wall temperatures for ARK_BC_NOSLIP_FIXED_T         */
+} ark_bc;
+
+typedef struct {
+    ark_grid grid;
+    ark_eos eos;
+    ark_gravity gravity;
+    double mu;                 /* dynamic viscosity; bulk viscosity eta = -2 mu / 3
+                                  (Stokes hypothesis, Eq. 4)                          */
+    double kappa;              /* heat conductivity, q = -kappa grad T (Eq. 3)        */
+    int low_mach;              /* 1: theta of Eq. 16; 0: theta = 1                    */
+    double K;                  /* a_{i+1/2} = K max(rho_i c_i, rho_{i+1} c_{i+1}),
+                                  K >= 1 (sub-characteristic condition, Sec. 2.1.2)   */
+    double cfl;                /* dt = cfl / max_i max(sum_d (|u_d| + c) / dx_d,
+                                  sum_d 2 max(4 mu / (3 rho), kappa (gamma - 1) / rho)
+                                  / dx_d^2)                                           */
+    ark_bc bc;
+    int precision;             /* ARK_F64, ARK_F32 or ARK_F32_SPLIT                   */
+} ark_params;
+
+typedef struct {
+    double mass;               /* sum rho dV                                          */
+    double momentum[3];        /* sum m dV                                            */
+    double energy;             /* sum rho*calE dV                                     */
+    double kinetic;            /* sum rho |u|^2 / 2 dV                                */
+    double max_speed;          /* max |u|                                             */
+    double mean_abs_v_last;    /* mean |u_last| (vertical velocity)                   */
+    double min_rho, min_p;
+    double t;                  /* simulated time                                      */
+    long long step;            /* steps taken                                         */
+    double dt;                 /* time step of the last step taken                    */
+    unsigned int status;       /* device status bits: 1 nonphysical rho/p, 2 L~ <= 0,
+                                  4 NaN; cleared by ark_set_state                     */
+} ark_diag;
+
+typedef struct ark_handle ark_handle;
+
+/* Create a solver for one grid.  Validates p (dims, sizes >= 1, n >= 2 along
+ * wall/outflow axes, gamma > 1, K >= 1, cfl > 0, mu, kappa >= 0, periodic
+ * axes without gravity; ARK_F32_SPLIT: fixed-temperature walls only at the
+ * two ends of the gravity axis), allocates the device state (two ping-pong copies of nf * N
+ * values of the chosen precision) and small scratch on the current device.
+ * The state is undefined until ark_set_state.  *out receives the handle,
+ * which the caller releases with ark_destroy.
+ * Errors: ARK_ERR_INVALID_ARG, ARK_ERR_UNSUPPORTED, ARK_ERR_ALLOC, ARK_ERR_CUDA. */
+ark_status ark_create(const ark_params* p, void* cuda_stream, ark_handle** out);
+
+/* Release every device and host resource of h (synchronises its stream). */
+ark_status ark_destroy(ark_handle* h);
+
+/* Load the state from U (nf * N FP64 values in the layout above), on the host
+ * (on_device = 0) or on the current device (on_device = 1).  For
+ * ARK_F32_SPLIT the FP64 base state is the horizontal mean of rho and p of
+ * each row along the gravity axis of U.  Resets t, step and status.  The
+ * caller keeps ownership of U; the call returns after U may be reused. */
+ark_status ark_set_state(ark_handle* h, const double* U, int on_device);
+
+/* Store the state into U (same layout, FP64), host or device memory. */
+ark_status ark_get_state(ark_handle* h, double* U, int on_device);
+
+/* CFL time step of the current state (formula at ark_params.cfl).  Writes it
+ * to *dt_out when dt_out != NULL (synchronising), and always leaves it on the
+ * device for the next ark_step with dt <= 0. */
+ark_status ark_compute_dt(ark_handle* h, double* dt_out);
+
+/* Advance nsteps >= 0 steps.  dt > 0: fixed time step.  dt <= 0: each step
+ * uses the CFL time step of its own initial state, reduced on the device by
+ * the previous step (the first from ark_compute_dt, run implicitly if
+ * needed).  One kernel launch per step; no host synchronisation. */
+ark_status ark_step(ark_handle* h, int nsteps, double dt);
+
+/* Conservation sums (FP64 tree sums in fixed order), extrema, t, step, dt and
+ * the device status word.  Synchronises.  Returns ARK_ERR_NONPHYSICAL (after
+ * filling *out) when the status word is non-zero. */
+ark_status ark_diagnostics(ark_handle* h, ark_diag* out);
+
+/* Simulated time and the time step of the last step taken (8 + 8 bytes read
+ * back from the device; synchronises the stream).  Either pointer may be NULL. */
+ark_status ark_time(ark_handle* h, double* t, double* dt);
+
+/* Wait for the handle's stream with a time limit (seconds); ARK_ERR_TIMEOUT
+ * when it is still busy at the limit, ARK_ERR_NONPHYSICAL when the device
+ * status word is non-zero, ARK_OK otherwise. */
+ark_status ark_sync(ark_handle* h, double timeout_s);
+
+/* Device address and byte size of the current state buffer (read only for
+ * the caller; valid until the next ark_step or ark_set_state). */
+ark_status ark_state_device_ptr(ark_handle* h, const void** ptr, size_t* bytes);
+
+/* Kernel shape chosen for h: in-plane tile (tx, ty), planes per block along
+ * the gravity axis, threads per block and blocks per launch. */
+ark_status ark_launch_shape(const ark_handle* h, int* tx, int* ty, int* planes, int* threads, int* blocks);
+
+const char* ark_last_error(const ark_handle* h);
+const char* ark_status_string(ark_status s);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* ARK_H */

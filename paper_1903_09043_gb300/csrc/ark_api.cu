@@ -1,0 +1,468 @@
+// ark_api.cu -- host implementation of the C ABI declared in include/ark.h.
+#include <chrono>
+#include <cmath>
+#include <cstdio>
+#include <cstring>
+#include <new>
+#include <string>
+#include <thread>
+#include <vector>
+
+#include "../../include/ark.h"
+#include "ark_aux.cuh"
+#include "ark_base.h"
+
+struct ark_handle {
+    ark_params p;
+    int dim = 2, nf = 4, prec = 0, visc = 0;
+    long long N = 0;
+    size_t esz = 8;
+    cudaStream_t stream = nullptr;
+    void* U[2] = {nullptr, nullptr};
+    int cur = 0;
+    void* base = nullptr;          // Real tables [NBASE][nv + 4]
+    double* base64 = nullptr;      // FP64 rho0, p0, W0 [3][nv + 4]
+    void* ctrl = nullptr;          // smax[3] | status | pad | time | dt_last | diag out[16] | partials
+    unsigned long long* smax = nullptr;
+    unsigned int* status = nullptr;
+    double* time = nullptr;
+    double* dt_last = nullptr;
+    double* diag_out = nullptr;
+    double* partials = nullptr;
+    long long step = 0;
+    bool dt_valid = false;
+    bool state_set = false;
+    ark::StepKernelInfo kinfo{};
+    dim3 grid;
+    int planes = 1, tiles_x = 1, tiles_y = 1;
+    std::string err;
+};
+
+namespace {
+
+ark_status fail(ark_handle* h, ark_status s, const std::string& msg)
+{
+    if (h) h->err = msg;
+    return s;
+}
+
+ark_status cuda_fail(ark_handle* h, cudaError_t e, const char* where)
+{
+    return fail(h, ARK_ERR_CUDA, std::string(where) + ": " + cudaGetErrorString(e));
+}
+
+#define ARK_CUDA(h, call)                                           \
+    do {                                                            \
+        cudaError_t e_ = (call);                                    \
+        if (e_ != cudaSuccess) return cuda_fail((h), e_, #call);    \
+    } while (0)
+
+int nv_of(const ark_handle* h) { return h->p.grid.n[h->dim - 1]; }
+
+ark::StepArgs base_args(const ark_handle* h)
+{
+    ark::StepArgs a;
+    std::memset(&a, 0, sizeof a);
+    const ark_params& p = h->p;
+    a.dim = h->dim;
+    for (int d = 0; d < 3; ++d) {
+        a.n[d] = d < h->dim ? p.grid.n[d] : 1;
+        a.dx[d] = d < h->dim ? (p.grid.hi[d] - p.grid.lo[d]) / p.grid.n[d] : 1.0;
+        a.bc_lo[d] = p.bc.lo[d];
+        a.bc_hi[d] = p.bc.hi[d];
+        a.Tw_lo[d] = p.bc.T_lo[d];
+        a.Tw_hi[d] = p.bc.T_hi[d];
+    }
+    a.gamma = p.eos.gamma;
+    a.g = p.gravity.g;
+    a.lo_v = p.grid.lo[h->dim - 1];
+    a.mu = p.mu;
+    a.kappa = p.kappa;
+    a.K = p.K;
+    a.cfl = p.cfl;
+    a.low_mach = p.low_mach;
+    a.planes = h->planes;
+    a.tiles_x = h->tiles_x;
+    a.tiles_y = h->tiles_y;
+    a.ncell = h->N;
+    a.base = h->base;
+    a.base64 = h->base64;
+    a.smax = h->smax;
+    a.status = h->status;
+    a.time = h->time;
+    a.dt_last = h->dt_last;
+    return a;
+}
+
+ark_status validate(const ark_params* p, std::string& msg)
+{
+    if (p->grid.dim != 2 && p->grid.dim != 3) { msg = "grid.dim must be 2 or 3"; return ARK_ERR_INVALID_ARG; }
+    const int dim = p->grid.dim;
+    for (int d = 0; d < dim; ++d) {
+        if (p->grid.n[d] < 1) { msg = "grid.n must be >= 1"; return ARK_ERR_INVALID_ARG; }
+        if (!(p->grid.hi[d] > p->grid.lo[d])) { msg = "grid.hi must exceed grid.lo"; return ARK_ERR_INVALID_ARG; }
+        for (int s = 0; s < 2; ++s) {
+            const int bc = s ? p->bc.hi[d] : p->bc.lo[d];
+            if (bc < ARK_BC_PERIODIC || bc > ARK_BC_OUTFLOW) { msg = "unknown boundary condition"; return ARK_ERR_INVALID_ARG; }
+            if (bc != ARK_BC_PERIODIC && p->grid.n[d] < 2) { msg = "walls and outflow need n >= 2 along their axis"; return ARK_ERR_INVALID_ARG; }
+            if (bc == ARK_BC_NOSLIP_FIXED_T && !((s ? p->bc.T_hi[d] : p->bc.T_lo[d]) > 0.0)) { msg = "wall temperature must be > 0"; return ARK_ERR_INVALID_ARG; }
+            if (bc == ARK_BC_NOSLIP_FIXED_T && p->precision == ARK_F32_SPLIT && d != dim - 1) {
+                msg = "ARK_F32_SPLIT supports fixed-temperature walls only across the gravity axis";
+                return ARK_ERR_UNSUPPORTED;
+            }
+        }
+        if ((p->bc.lo[d] == ARK_BC_PERIODIC) != (p->bc.hi[d] == ARK_BC_PERIODIC)) {
+            msg = "periodic boundaries come in pairs"; return ARK_ERR_INVALID_ARG;
+        }
+    }
+    if (p->bc.lo[dim - 1] == ARK_BC_PERIODIC && p->gravity.g != 0.0) {
+        msg = "gravity along a periodic axis"; return ARK_ERR_INVALID_ARG;
+    }
+    if (!(p->eos.gamma > 1.0)) { msg = "eos.gamma must be > 1"; return ARK_ERR_INVALID_ARG; }
+    if (!(p->K >= 1.0)) { msg = "K must be >= 1 (sub-characteristic condition)"; return ARK_ERR_INVALID_ARG; }
+    if (!(p->cfl > 0.0)) { msg = "cfl must be > 0"; return ARK_ERR_INVALID_ARG; }
+    if (!(p->mu >= 0.0) || !(p->kappa >= 0.0)) { msg = "mu and kappa must be >= 0"; return ARK_ERR_INVALID_ARG; }
+    if (p->precision < ARK_F64 || p->precision > ARK_F32_SPLIT) { msg = "unknown precision"; return ARK_ERR_INVALID_ARG; }
+    if (p->low_mach != 0 && p->low_mach != 1) { msg = "low_mach must be 0 or 1"; return ARK_ERR_INVALID_ARG; }
+    return ARK_OK;
+}
+
+void choose_launch(ark_handle* h, int nsm)
+{
+    const int dim = h->dim;
+    h->kinfo = dim == 2 ? ark::step_kernel_2d(h->prec, h->visc) : ark::step_kernel_3d(h->prec, h->visc);
+    h->tiles_x = (h->p.grid.n[0] + h->kinfo.tx - 1) / h->kinfo.tx;
+    h->tiles_y = dim == 3 ? (h->p.grid.n[1] + h->kinfo.ty - 1) / h->kinfo.ty : 1;
+    const int tiles = h->tiles_x * h->tiles_y;
+    const int nv = nv_of(h);
+    // enough blocks for ~4 waves of resident blocks, each marching >= 8 planes
+    const long long want = 4LL * nsm * h->kinfo.blocks_per_sm;
+    long long chunks = (want + tiles - 1) / tiles;
+    const long long maxc = (nv + 7) / 8;
+    if (chunks > maxc) chunks = maxc;
+    if (chunks < 1) chunks = 1;
+    h->planes = (int)((nv + chunks - 1) / chunks);
+    const int nchunk = (nv + h->planes - 1) / h->planes;
+    h->grid = dim3(tiles, nchunk, 1);
+}
+
+ark_status ensure_dt(ark_handle* h)
+{
+    if (h->dt_valid) return ARK_OK;
+    unsigned long long* slot = h->smax + (h->step % 3);
+    ARK_CUDA(h, cudaMemsetAsync(slot, 0, sizeof(unsigned long long), h->stream));
+    ark::StepArgs a = base_args(h);
+    ARK_CUDA(h, ark::launch_wave_rate(a, h->prec, h->visc, h->U[h->cur], slot, h->stream));
+    h->dt_valid = true;
+    return ARK_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+const char* ark_status_string(ark_status s)
+{
+    switch (s) {
+    case ARK_OK: return "ok";
+    case ARK_ERR_INVALID_ARG: return "invalid argument";
+    case ARK_ERR_CUDA: return "CUDA error";
+    case ARK_ERR_NONPHYSICAL: return "nonphysical state";
+    case ARK_ERR_TIMEOUT: return "timeout";
+    case ARK_ERR_UNSUPPORTED: return "unsupported";
+    case ARK_ERR_ALLOC: return "allocation failed";
+    }
+    return "unknown status";
+}
+
+const char* ark_last_error(const ark_handle* h) { return h ? h->err.c_str() : "null handle"; }
+
+ark_status ark_create(const ark_params* p, void* cuda_stream, ark_handle** out)
+{
+    if (!p || !out) return ARK_ERR_INVALID_ARG;
+    *out = nullptr;
+    std::string msg;
+    ark_status st = validate(p, msg);
+    if (st != ARK_OK) return st;
+    ark_handle* h = new (std::nothrow) ark_handle();
+    if (!h) return ARK_ERR_ALLOC;
+    h->p = *p;
+    h->dim = p->grid.dim;
+    h->nf = h->dim + 2;
+    h->prec = p->precision;
+    h->visc = (p->mu > 0.0 || p->kappa > 0.0) ? 1 : 0;
+    if (h->dim == 2) h->p.grid.n[2] = 1;
+    h->N = (long long)h->p.grid.n[0] * h->p.grid.n[1] * h->p.grid.n[2];
+    h->esz = h->prec == ARK_F64 ? 8 : 4;
+    h->stream = (cudaStream_t)cuda_stream;
+
+    int dev = 0, nsm = 0;
+    cudaError_t e = cudaGetDevice(&dev);
+    if (e == cudaSuccess) e = cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev);
+    if (e != cudaSuccess) { st = cuda_fail(h, e, "device query"); delete h; return st; }
+
+    const size_t bytes = (size_t)h->nf * h->N * h->esz;
+    const int L = nv_of(h) + 4;
+    const size_t ctrl_bytes = 64 + 64 + 16 * 8 + (size_t)ark::DIAG_BLOCKS * ark::DG_NTOT * 8;
+    if (cudaMalloc(&h->U[0], bytes) != cudaSuccess || cudaMalloc(&h->U[1], bytes) != cudaSuccess ||
+        cudaMalloc(&h->ctrl, ctrl_bytes) != cudaSuccess ||
+        (h->prec == ARK_F32_SPLIT && (cudaMalloc(&h->base, (size_t)ark::NBASE * L * sizeof(float)) != cudaSuccess ||
+                                      cudaMalloc((void**)&h->base64, 3 * (size_t)L * sizeof(double)) != cudaSuccess))) {
+        cudaGetLastError();
+        ark_destroy(h);
+        return ARK_ERR_ALLOC;
+    }
+    char* c = (char*)h->ctrl;
+    h->smax = (unsigned long long*)c;              // 3 slots
+    h->status = (unsigned int*)(c + 32);
+    h->time = (double*)(c + 64);
+    h->dt_last = (double*)(c + 72);
+    h->diag_out = (double*)(c + 128);
+    h->partials = (double*)(c + 128 + 16 * 8);
+    e = cudaMemsetAsync(h->ctrl, 0, ctrl_bytes, h->stream);
+    if (e != cudaSuccess) { st = cuda_fail(h, e, "cudaMemsetAsync"); ark_destroy(h); return st; }
+    choose_launch(h, nsm);
+    *out = h;
+    return ARK_OK;
+}
+
+ark_status ark_destroy(ark_handle* h)
+{
+    if (!h) return ARK_ERR_INVALID_ARG;
+    if (h->stream || h->U[0]) cudaStreamSynchronize(h->stream);
+    cudaFree(h->U[0]);
+    cudaFree(h->U[1]);
+    cudaFree(h->ctrl);
+    cudaFree(h->base);
+    cudaFree(h->base64);
+    delete h;
+    return ARK_OK;
+}
+
+ark_status ark_set_state(ark_handle* h, const double* U, int on_device)
+{
+    if (!h || !U) return fail(h, ARK_ERR_INVALID_ARG, "null argument");
+    const size_t bytes64 = (size_t)h->nf * h->N * sizeof(double);
+    const double* src = U;
+    double* tmp = nullptr;
+    if (!on_device) {
+        if (h->prec == ARK_F64) {
+            ARK_CUDA(h, cudaMemcpyAsync(h->U[h->cur], U, bytes64, cudaMemcpyHostToDevice, h->stream));
+        } else {
+            if (cudaMallocAsync((void**)&tmp, bytes64, h->stream) != cudaSuccess) {
+                cudaGetLastError();
+                return fail(h, ARK_ERR_ALLOC, "staging buffer");
+            }
+            ARK_CUDA(h, cudaMemcpyAsync(tmp, U, bytes64, cudaMemcpyHostToDevice, h->stream));
+            src = tmp;
+        }
+    } else if (h->prec == ARK_F64) {
+        ARK_CUDA(h, cudaMemcpyAsync(h->U[h->cur], U, bytes64, cudaMemcpyDeviceToDevice, h->stream));
+    }
+    ark::StepArgs a = base_args(h);
+    ark_status st = ARK_OK;
+    if (h->prec == ARK_F32_SPLIT) {
+        const int nv = nv_of(h), L = nv + 4;
+        double* means = nullptr;
+        cudaError_t e = cudaMallocAsync((void**)&means, 2 * (size_t)nv * sizeof(double), h->stream);
+        if (e == cudaSuccess) e = ark::launch_row_means(a, src, means, means + nv, h->stream);
+        std::vector<double> hm(2 * (size_t)nv);
+        if (e == cudaSuccess) e = cudaMemcpyAsync(hm.data(), means, hm.size() * sizeof(double), cudaMemcpyDeviceToHost, h->stream);
+        if (e == cudaSuccess) e = cudaStreamSynchronize(h->stream);
+        if (means) cudaFreeAsync(means, h->stream);
+        if (e != cudaSuccess) { if (tmp) cudaFreeAsync(tmp, h->stream); return cuda_fail(h, e, "base state"); }
+        std::vector<double> rho(hm.begin(), hm.begin() + nv), pr(hm.begin() + nv, hm.end());
+        for (int r = 0; r < nv; ++r)
+            if (!(rho[r] > 0.0) || !(pr[r] > 0.0)) {
+                if (tmp) cudaFreeAsync(tmp, h->stream);
+                return fail(h, ARK_ERR_NONPHYSICAL, "base state with rho <= 0 or p <= 0");
+            }
+        std::vector<double> b64;
+        std::vector<float> tab;
+        {
+            const ark_params& p = h->p;
+            const int V = h->dim - 1;
+            ark::BaseSpec bs{nv, p.grid.lo[V], (p.grid.hi[V] - p.grid.lo[V]) / nv, p.gravity.g, p.eos.gamma, p.kappa,
+                             p.bc.lo[V], p.bc.hi[V], p.bc.T_lo[V], p.bc.T_hi[V]};
+            ark::build_base_tables(bs, rho, pr, b64, tab);
+        }
+        e = cudaMemcpyAsync(h->base64, b64.data(), b64.size() * sizeof(double), cudaMemcpyHostToDevice, h->stream);
+        if (e == cudaSuccess) e = cudaMemcpyAsync(h->base, tab.data(), tab.size() * sizeof(float), cudaMemcpyHostToDevice, h->stream);
+        if (e == cudaSuccess) e = cudaStreamSynchronize(h->stream);   // host vectors leave scope
+        if (e != cudaSuccess) { if (tmp) cudaFreeAsync(tmp, h->stream); return cuda_fail(h, e, "base tables"); }
+        (void)L;
+    }
+    if (h->prec != ARK_F64) {
+        cudaError_t e = ark::launch_convert_in(a, h->prec, src, h->U[h->cur], h->stream);
+        if (e != cudaSuccess) st = cuda_fail(h, e, "convert_in");
+    }
+    if (tmp) cudaFreeAsync(tmp, h->stream);
+    if (st != ARK_OK) return st;
+    ARK_CUDA(h, cudaMemsetAsync(h->ctrl, 0, 128, h->stream));   // smax slots, status, time, dt
+    h->step = 0;
+    h->dt_valid = false;
+    h->state_set = true;
+    if (!on_device) ARK_CUDA(h, cudaStreamSynchronize(h->stream));   // caller may reuse U
+    return ARK_OK;
+}
+
+ark_status ark_get_state(ark_handle* h, double* U, int on_device)
+{
+    if (!h || !U) return fail(h, ARK_ERR_INVALID_ARG, "null argument");
+    if (!h->state_set) return fail(h, ARK_ERR_INVALID_ARG, "state not set");
+    const size_t bytes64 = (size_t)h->nf * h->N * sizeof(double);
+    if (h->prec == ARK_F64) {
+        ARK_CUDA(h, cudaMemcpyAsync(U, h->U[h->cur], bytes64, on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost,
+                                    h->stream));
+    } else {
+        ark::StepArgs a = base_args(h);
+        double* dst = U;
+        double* tmp = nullptr;
+        if (!on_device) {
+            if (cudaMallocAsync((void**)&tmp, bytes64, h->stream) != cudaSuccess) {
+                cudaGetLastError();
+                return fail(h, ARK_ERR_ALLOC, "staging buffer");
+            }
+            dst = tmp;
+        }
+        cudaError_t e = ark::launch_convert_out(a, h->prec, h->U[h->cur], dst, h->stream);
+        if (e == cudaSuccess && tmp) e = cudaMemcpyAsync(U, tmp, bytes64, cudaMemcpyDeviceToHost, h->stream);
+        if (tmp) cudaFreeAsync(tmp, h->stream);
+        if (e != cudaSuccess) return cuda_fail(h, e, "get_state");
+    }
+    if (!on_device) ARK_CUDA(h, cudaStreamSynchronize(h->stream));
+    return ARK_OK;
+}
+
+ark_status ark_compute_dt(ark_handle* h, double* dt_out)
+{
+    if (!h) return ARK_ERR_INVALID_ARG;
+    if (!h->state_set) return fail(h, ARK_ERR_INVALID_ARG, "state not set");
+    h->dt_valid = false;
+    ark_status st = ensure_dt(h);
+    if (st != ARK_OK) return st;
+    if (dt_out) {
+        unsigned long long bits = 0;
+        ARK_CUDA(h, cudaMemcpyAsync(&bits, h->smax + (h->step % 3), sizeof bits, cudaMemcpyDeviceToHost, h->stream));
+        ARK_CUDA(h, cudaStreamSynchronize(h->stream));
+        double s;
+        std::memcpy(&s, &bits, sizeof s);
+        *dt_out = h->p.cfl / s;
+    }
+    return ARK_OK;
+}
+
+ark_status ark_step(ark_handle* h, int nsteps, double dt)
+{
+    if (!h || nsteps < 0) return fail(h, ARK_ERR_INVALID_ARG, "bad arguments");
+    if (!h->state_set) return fail(h, ARK_ERR_INVALID_ARG, "state not set");
+    if (nsteps == 0) return ARK_OK;
+    if (!(dt > 0.0)) {
+        ark_status st = ensure_dt(h);
+        if (st != ARK_OK) return st;
+    }
+    ark::StepArgs a = base_args(h);
+    a.dt_fixed = dt > 0.0 ? dt : 0.0;
+    for (int i = 0; i < nsteps; ++i) {
+        const long long n = h->step;
+        a.Uin = h->U[h->cur];
+        a.Uout = h->U[1 - h->cur];
+        a.slot_read = (int)(n % 3);
+        a.slot_write = (int)((n + 1) % 3);
+        a.slot_reset = (int)((n + 2) % 3);
+        cudaError_t e = h->kinfo.launch(a, h->grid, h->stream);
+        if (e != cudaSuccess) return cuda_fail(h, e, "step launch");
+        h->cur = 1 - h->cur;
+        h->step = n + 1;
+    }
+    h->dt_valid = true;   // every step leaves the next step's wave rate in its slot
+    return ARK_OK;
+}
+
+ark_status ark_diagnostics(ark_handle* h, ark_diag* out)
+{
+    if (!h || !out) return fail(h, ARK_ERR_INVALID_ARG, "null argument");
+    if (!h->state_set) return fail(h, ARK_ERR_INVALID_ARG, "state not set");
+    ark::StepArgs a = base_args(h);
+    ARK_CUDA(h, ark::launch_diagnostics(a, h->prec, h->U[h->cur], h->partials, h->diag_out, h->stream));
+    double v[16];
+    unsigned char ctrl[128];
+    ARK_CUDA(h, cudaMemcpyAsync(v, h->diag_out, sizeof v, cudaMemcpyDeviceToHost, h->stream));
+    ARK_CUDA(h, cudaMemcpyAsync(ctrl, h->ctrl, sizeof ctrl, cudaMemcpyDeviceToHost, h->stream));
+    ARK_CUDA(h, cudaStreamSynchronize(h->stream));
+    double vol = 1.0;
+    for (int d = 0; d < h->dim; ++d) vol *= (h->p.grid.hi[d] - h->p.grid.lo[d]) / h->p.grid.n[d];
+    std::memset(out, 0, sizeof *out);
+    out->mass = v[ark::DG_MASS] * vol;
+    out->momentum[0] = v[ark::DG_MX] * vol;
+    out->momentum[1] = v[ark::DG_MY] * vol;
+    out->momentum[2] = v[ark::DG_MZ] * vol;
+    out->energy = v[ark::DG_W] * vol;
+    out->kinetic = v[ark::DG_KE] * vol;
+    out->max_speed = v[ark::DG_UMAX];
+    out->mean_abs_v_last = v[ark::DG_VABS] / (double)h->N;
+    out->min_rho = v[ark::DG_RMIN];
+    out->min_p = v[ark::DG_PMIN];
+    std::memcpy(&out->status, ctrl + 32, sizeof(unsigned));
+    std::memcpy(&out->t, ctrl + 64, sizeof(double));
+    std::memcpy(&out->dt, ctrl + 72, sizeof(double));
+    out->step = h->step;
+    if (v[ark::DG_NAN] > 0.0) out->status |= ark::ST_NAN;
+    if (out->status) return fail(h, ARK_ERR_NONPHYSICAL, "device reported a nonphysical state");
+    return ARK_OK;
+}
+
+ark_status ark_time(ark_handle* h, double* t, double* dt)
+{
+    if (!h) return ARK_ERR_INVALID_ARG;
+    double v[2];
+    ARK_CUDA(h, cudaMemcpyAsync(v, h->time, sizeof v, cudaMemcpyDeviceToHost, h->stream));
+    ARK_CUDA(h, cudaStreamSynchronize(h->stream));
+    if (t) *t = v[0];
+    if (dt) *dt = v[1];
+    return ARK_OK;
+}
+
+ark_status ark_sync(ark_handle* h, double timeout_s)
+{
+    if (!h) return ARK_ERR_INVALID_ARG;
+    cudaEvent_t ev;
+    ARK_CUDA(h, cudaEventCreateWithFlags(&ev, cudaEventDisableTiming));
+    cudaError_t e = cudaEventRecord(ev, h->stream);
+    if (e != cudaSuccess) { cudaEventDestroy(ev); return cuda_fail(h, e, "cudaEventRecord"); }
+    const auto t0 = std::chrono::steady_clock::now();
+    for (;;) {
+        e = cudaEventQuery(ev);
+        if (e == cudaSuccess) break;
+        if (e != cudaErrorNotReady) { cudaEventDestroy(ev); return cuda_fail(h, e, "cudaEventQuery"); }
+        const double el = std::chrono::duration<double>(std::chrono::steady_clock::now() - t0).count();
+        if (el > timeout_s) { cudaEventDestroy(ev); return fail(h, ARK_ERR_TIMEOUT, "stream still busy"); }
+        std::this_thread::sleep_for(std::chrono::microseconds(50));
+    }
+    cudaEventDestroy(ev);
+    unsigned status = 0;
+    ARK_CUDA(h, cudaMemcpy(&status, h->status, sizeof status, cudaMemcpyDeviceToHost));
+    if (status) return fail(h, ARK_ERR_NONPHYSICAL, "device reported a nonphysical state");
+    return ARK_OK;
+}
+
+ark_status ark_state_device_ptr(ark_handle* h, const void** ptr, size_t* bytes)
+{
+    if (!h || !ptr || !bytes) return fail(h, ARK_ERR_INVALID_ARG, "null argument");
+    *ptr = h->U[h->cur];
+    *bytes = (size_t)h->nf * h->N * h->esz;
+    return ARK_OK;
+}
+
+ark_status ark_launch_shape(const ark_handle* h, int* tx, int* ty, int* planes, int* threads, int* blocks)
+{
+    if (!h) return ARK_ERR_INVALID_ARG;
+    if (tx) *tx = h->kinfo.tx;
+    if (ty) *ty = h->kinfo.ty;
+    if (planes) *planes = h->planes;
+    if (threads) *threads = h->kinfo.threads;
+    if (blocks) *blocks = (int)(h->grid.x * h->grid.y);
+    return ARK_OK;
+}
+
+}  // extern "C"

@@ -1,0 +1,294 @@
+// ark_aux.cu -- CFL wave-rate reduction, state conversion, base-state row
+// means and conservation diagnostics (GB300, sm_103a).
+#include "ark_aux.cuh"
+#include "ark_step.cuh"
+
+namespace ark {
+
+namespace {
+
+constexpr int AUX_THREADS = 256;
+
+__device__ __forceinline__ int row_of(const StepArgs& a, long long idx)
+{
+    const long long plane = a.dim == 3 ? (long long)a.n[0] * a.n[1] : (long long)a.n[0];
+    return (int)(idx / plane);
+}
+
+template <typename T>
+__device__ __forceinline__ void block_reduce_max(T& v, double* red)
+{
+    red[threadIdx.x] = double(v);
+    __syncthreads();
+    for (int s = AUX_THREADS / 2; s > 0; s >>= 1) {
+        if (threadIdx.x < s) red[threadIdx.x] = fmax(red[threadIdx.x], red[threadIdx.x + s]);
+        __syncthreads();
+    }
+}
+
+// Wave rate of every cell; one atomicMax per block on the FP64 bit pattern
+// (positive doubles order like their bit patterns, so the result does not
+// depend on the order of the blocks).
+template <int D, typename Real, bool SPLIT, bool VISC>
+__global__ void __launch_bounds__(AUX_THREADS) wave_rate_kernel(const StepArgs a, const Real* __restrict__ U,
+                                                                  unsigned long long* slot)
+{
+    __shared__ double red[AUX_THREADS];
+    const int nv = a.n[D - 1];
+    const double dv = a.dx[D - 1];
+    const Real gamma = Real(a.gamma), gm1 = Real(a.gamma - 1.0), mu = Real(a.mu), kappa = Real(a.kappa);
+    const Real invdx[3] = {Real(1.0 / a.dx[0]), Real(1.0 / a.dx[1]), Real(1.0 / a.dx[2])};
+    Real smax = Real(0);
+    for (long long idx = blockIdx.x * (long long)blockDim.x + threadIdx.x; idx < a.ncell;
+         idx += (long long)gridDim.x * blockDim.x) {
+        Real b[D + 2];
+#pragma unroll
+        for (int k = 0; k < D + 2; ++k) b[k] = __ldg(U + k * a.ncell + idx);
+        const Row<Real> w = row_info<Real, SPLIT>(a, row_of(a, idx), nv, dv);
+        Real p, rho;
+        const Real sh = wave_rate<D, Real, SPLIT, VISC>(b, w, gm1, gamma, invdx, mu, kappa, p, rho);
+        if (!(sh <= smax)) smax = (sh == sh) ? sh : smax;
+    }
+    block_reduce_max(smax, red);
+    if (threadIdx.x == 0) atomicMax(slot, (unsigned long long)__double_as_longlong(red[0]));
+}
+
+template <int D, typename Real, bool SPLIT>
+__global__ void __launch_bounds__(AUX_THREADS) convert_in_kernel(const StepArgs a, const double* __restrict__ Uin,
+                                                                   Real* __restrict__ Uout)
+{
+    const int nv = a.n[D - 1];
+    for (long long idx = blockIdx.x * (long long)blockDim.x + threadIdx.x; idx < a.ncell;
+         idx += (long long)gridDim.x * blockDim.x) {
+        const int r = row_of(a, idx);
+        double rho = Uin[idx], W = Uin[(D + 1) * a.ncell + idx];
+        if constexpr (SPLIT) {
+            rho -= a.base64[0 * (nv + 4) + r + 2];
+            W -= a.base64[2 * (nv + 4) + r + 2];
+        }
+        Uout[idx] = Real(rho);
+#pragma unroll
+        for (int d = 0; d < D; ++d) Uout[(1 + d) * a.ncell + idx] = Real(Uin[(1 + d) * a.ncell + idx]);
+        Uout[(D + 1) * a.ncell + idx] = Real(W);
+    }
+}
+
+template <int D, typename Real, bool SPLIT>
+__global__ void __launch_bounds__(AUX_THREADS) convert_out_kernel(const StepArgs a, const Real* __restrict__ Uin,
+                                                                    double* __restrict__ Uout)
+{
+    const int nv = a.n[D - 1];
+    for (long long idx = blockIdx.x * (long long)blockDim.x + threadIdx.x; idx < a.ncell;
+         idx += (long long)gridDim.x * blockDim.x) {
+        const int r = row_of(a, idx);
+        double rho = double(Uin[idx]), W = double(Uin[(D + 1) * a.ncell + idx]);
+        if constexpr (SPLIT) {
+            rho += a.base64[0 * (nv + 4) + r + 2];
+            W += a.base64[2 * (nv + 4) + r + 2];
+        }
+        Uout[idx] = rho;
+#pragma unroll
+        for (int d = 0; d < D; ++d) Uout[(1 + d) * a.ncell + idx] = double(Uin[(1 + d) * a.ncell + idx]);
+        Uout[(D + 1) * a.ncell + idx] = W;
+    }
+}
+
+// One block per row of the last axis; fixed-order tree sums.
+template <int D>
+__global__ void __launch_bounds__(AUX_THREADS) row_means_kernel(const StepArgs a, const double* __restrict__ U,
+                                                                  double* rho_mean, double* p_mean)
+{
+    __shared__ double sr[AUX_THREADS], sp[AUX_THREADS];
+    const int r = blockIdx.x;
+    const long long plane = D == 3 ? (long long)a.n[0] * a.n[1] : (long long)a.n[0];
+    const double phi = -(a.g * (a.lo_v + (r + 0.5) * a.dx[D - 1]));
+    double accr = 0.0, accp = 0.0;
+    for (long long i = threadIdx.x; i < plane; i += AUX_THREADS) {
+        const long long idx = r * plane + i;
+        const double rho = U[idx];
+        double ke = 0.0;
+#pragma unroll
+        for (int d = 0; d < D; ++d) {
+            const double m = U[(1 + d) * a.ncell + idx];
+            ke += 0.5 * m * m / rho;
+        }
+        accr += rho;
+        accp += (a.gamma - 1.0) * (U[(D + 1) * a.ncell + idx] - ke - rho * phi);
+    }
+    sr[threadIdx.x] = accr;
+    sp[threadIdx.x] = accp;
+    __syncthreads();
+    for (int s = AUX_THREADS / 2; s > 0; s >>= 1) {
+        if (threadIdx.x < s) {
+            sr[threadIdx.x] += sr[threadIdx.x + s];
+            sp[threadIdx.x] += sp[threadIdx.x + s];
+        }
+        __syncthreads();
+    }
+    if (threadIdx.x == 0) {
+        rho_mean[r] = sr[0] / double(plane);
+        p_mean[r] = sp[0] / double(plane);
+    }
+}
+
+template <int D, typename Real, bool SPLIT>
+__global__ void __launch_bounds__(AUX_THREADS) diag_kernel(const StepArgs a, const Real* __restrict__ U,
+                                                             double* partials)
+{
+    __shared__ double red[DG_NTOT][AUX_THREADS];
+    const int nv = a.n[D - 1];
+    double acc[DG_NTOT];
+#pragma unroll
+    for (int k = 0; k < DG_NSUM; ++k) acc[k] = 0.0;
+    acc[DG_UMAX] = 0.0;
+    acc[DG_RMIN] = INFINITY;
+    acc[DG_PMIN] = INFINITY;
+    acc[DG_NAN] = 0.0;
+    for (long long idx = blockIdx.x * (long long)blockDim.x + threadIdx.x; idx < a.ncell;
+         idx += (long long)gridDim.x * blockDim.x) {
+        const int r = row_of(a, idx);
+        const double phi = -(a.g * (a.lo_v + (r + 0.5) * a.dx[D - 1]));
+        double rho = double(U[idx]), W = double(U[(D + 1) * a.ncell + idx]);
+        if constexpr (SPLIT) {
+            rho += a.base64[0 * (nv + 4) + r + 2];
+            W += a.base64[2 * (nv + 4) + r + 2];
+        }
+        double m[3] = {0.0, 0.0, 0.0}, ke = 0.0, u2 = 0.0;
+#pragma unroll
+        for (int d = 0; d < D; ++d) {
+            m[d] = double(U[(1 + d) * a.ncell + idx]);
+            const double u = m[d] / rho;
+            ke += 0.5 * rho * u * u;
+            u2 += u * u;
+        }
+        const double p = (a.gamma - 1.0) * (W - ke - rho * phi);
+        acc[DG_MASS] += rho;
+        acc[DG_MX] += m[0];
+        acc[DG_MY] += m[1];
+        acc[DG_MZ] += m[2];
+        acc[DG_W] += W;
+        acc[DG_KE] += ke;
+        acc[DG_VABS] += fabs(m[D - 1] / rho);
+        acc[DG_UMAX] = fmax(acc[DG_UMAX], sqrt(u2));
+        acc[DG_RMIN] = fmin(acc[DG_RMIN], rho);
+        acc[DG_PMIN] = fmin(acc[DG_PMIN], p);
+        if (!(p == p) || !(rho == rho) || !(W == W)) acc[DG_NAN] += 1.0;
+    }
+#pragma unroll
+    for (int k = 0; k < DG_NTOT; ++k) red[k][threadIdx.x] = acc[k];
+    __syncthreads();
+    for (int s = AUX_THREADS / 2; s > 0; s >>= 1) {
+        if (threadIdx.x < s) {
+#pragma unroll
+            for (int k = 0; k < DG_NSUM; ++k) red[k][threadIdx.x] += red[k][threadIdx.x + s];
+            red[DG_UMAX][threadIdx.x] = fmax(red[DG_UMAX][threadIdx.x], red[DG_UMAX][threadIdx.x + s]);
+            red[DG_RMIN][threadIdx.x] = fmin(red[DG_RMIN][threadIdx.x], red[DG_RMIN][threadIdx.x + s]);
+            red[DG_PMIN][threadIdx.x] = fmin(red[DG_PMIN][threadIdx.x], red[DG_PMIN][threadIdx.x + s]);
+            red[DG_NAN][threadIdx.x] += red[DG_NAN][threadIdx.x + s];
+        }
+        __syncthreads();
+    }
+    if (threadIdx.x < DG_NTOT) partials[blockIdx.x * DG_NTOT + threadIdx.x] = red[threadIdx.x][0];
+}
+
+__global__ void diag_final_kernel(const double* partials, int nblocks, double* out)
+{
+    // one thread per quantity, blocks in index order: a fixed summation order
+    const int k = threadIdx.x;
+    if (k >= DG_NTOT) return;
+    double v = partials[k];
+    for (int b = 1; b < nblocks; ++b) {
+        const double x = partials[b * DG_NTOT + k];
+        if (k < DG_NSUM || k == DG_NAN) v += x;
+        else if (k == DG_UMAX) v = fmax(v, x);
+        else v = fmin(v, x);
+    }
+    out[k] = v;
+}
+
+int grid_for(long long n)
+{
+    long long b = (n + AUX_THREADS - 1) / AUX_THREADS;
+    if (b > 152 * 16) b = 152 * 16;
+    if (b < 1) b = 1;
+    return (int)b;
+}
+
+}  // namespace
+
+cudaError_t launch_wave_rate(const StepArgs& a, int prec, int visc, const void* U, unsigned long long* slot,
+                             cudaStream_t s)
+{
+    const int g = grid_for(a.ncell);
+#define ARK_WR(D, R, SP, VI) wave_rate_kernel<D, R, SP, VI><<<g, AUX_THREADS, 0, s>>>(a, (const R*)U, slot)
+    if (a.dim == 2) {
+        if (prec == P_F64) { if (visc) ARK_WR(2, double, false, true); else ARK_WR(2, double, false, false); }
+        else if (prec == P_F32) { if (visc) ARK_WR(2, float, false, true); else ARK_WR(2, float, false, false); }
+        else { if (visc) ARK_WR(2, float, true, true); else ARK_WR(2, float, true, false); }
+    } else {
+        if (prec == P_F64) { if (visc) ARK_WR(3, double, false, true); else ARK_WR(3, double, false, false); }
+        else if (prec == P_F32) { if (visc) ARK_WR(3, float, false, true); else ARK_WR(3, float, false, false); }
+        else { if (visc) ARK_WR(3, float, true, true); else ARK_WR(3, float, true, false); }
+    }
+#undef ARK_WR
+    return cudaGetLastError();
+}
+
+cudaError_t launch_convert_in(const StepArgs& a, int prec, const double* Uin, void* Uout, cudaStream_t s)
+{
+    const int g = grid_for(a.ncell);
+    if (a.dim == 2) {
+        if (prec == P_F64) convert_in_kernel<2, double, false><<<g, AUX_THREADS, 0, s>>>(a, Uin, (double*)Uout);
+        else if (prec == P_F32) convert_in_kernel<2, float, false><<<g, AUX_THREADS, 0, s>>>(a, Uin, (float*)Uout);
+        else convert_in_kernel<2, float, true><<<g, AUX_THREADS, 0, s>>>(a, Uin, (float*)Uout);
+    } else {
+        if (prec == P_F64) convert_in_kernel<3, double, false><<<g, AUX_THREADS, 0, s>>>(a, Uin, (double*)Uout);
+        else if (prec == P_F32) convert_in_kernel<3, float, false><<<g, AUX_THREADS, 0, s>>>(a, Uin, (float*)Uout);
+        else convert_in_kernel<3, float, true><<<g, AUX_THREADS, 0, s>>>(a, Uin, (float*)Uout);
+    }
+    return cudaGetLastError();
+}
+
+cudaError_t launch_convert_out(const StepArgs& a, int prec, const void* Uin, double* Uout, cudaStream_t s)
+{
+    const int g = grid_for(a.ncell);
+    if (a.dim == 2) {
+        if (prec == P_F64) convert_out_kernel<2, double, false><<<g, AUX_THREADS, 0, s>>>(a, (const double*)Uin, Uout);
+        else if (prec == P_F32) convert_out_kernel<2, float, false><<<g, AUX_THREADS, 0, s>>>(a, (const float*)Uin, Uout);
+        else convert_out_kernel<2, float, true><<<g, AUX_THREADS, 0, s>>>(a, (const float*)Uin, Uout);
+    } else {
+        if (prec == P_F64) convert_out_kernel<3, double, false><<<g, AUX_THREADS, 0, s>>>(a, (const double*)Uin, Uout);
+        else if (prec == P_F32) convert_out_kernel<3, float, false><<<g, AUX_THREADS, 0, s>>>(a, (const float*)Uin, Uout);
+        else convert_out_kernel<3, float, true><<<g, AUX_THREADS, 0, s>>>(a, (const float*)Uin, Uout);
+    }
+    return cudaGetLastError();
+}
+
+cudaError_t launch_row_means(const StepArgs& a, const double* U, double* rho_mean, double* p_mean, cudaStream_t s)
+{
+    const int nv = a.n[a.dim - 1];
+    if (a.dim == 2) row_means_kernel<2><<<nv, AUX_THREADS, 0, s>>>(a, U, rho_mean, p_mean);
+    else row_means_kernel<3><<<nv, AUX_THREADS, 0, s>>>(a, U, rho_mean, p_mean);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_diagnostics(const StepArgs& a, int prec, const void* U, double* partials, double* out,
+                               cudaStream_t s)
+{
+    const int g = DIAG_BLOCKS;
+    if (a.dim == 2) {
+        if (prec == P_F64) diag_kernel<2, double, false><<<g, AUX_THREADS, 0, s>>>(a, (const double*)U, partials);
+        else if (prec == P_F32) diag_kernel<2, float, false><<<g, AUX_THREADS, 0, s>>>(a, (const float*)U, partials);
+        else diag_kernel<2, float, true><<<g, AUX_THREADS, 0, s>>>(a, (const float*)U, partials);
+    } else {
+        if (prec == P_F64) diag_kernel<3, double, false><<<g, AUX_THREADS, 0, s>>>(a, (const double*)U, partials);
+        else if (prec == P_F32) diag_kernel<3, float, false><<<g, AUX_THREADS, 0, s>>>(a, (const float*)U, partials);
+        else diag_kernel<3, float, true><<<g, AUX_THREADS, 0, s>>>(a, (const float*)U, partials);
+    }
+    cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess) return e;
+    diag_final_kernel<<<1, 32, 0, s>>>(partials, g, out);
+    return cudaGetLastError();
+}
+
+}  // namespace ark

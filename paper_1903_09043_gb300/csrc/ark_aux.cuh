@@ -1,0 +1,40 @@
+// ark_aux.cuh -- launchers of the non-step kernels and lookup of the step
+// kernel instances, used by the host API.
+#pragma once
+
+#include <cuda_runtime.h>
+
+#include "ark_common.cuh"
+
+namespace ark {
+
+// CFL wave rate max over all cells of U -> atomicMax into *slot (FP64 bits).
+cudaError_t launch_wave_rate(const StepArgs& a, int prec, int visc, const void* U, unsigned long long* slot,
+                             cudaStream_t s);
+
+// FP64 full state (device) -> storage state (deviation form for F32_SPLIT), and back.
+cudaError_t launch_convert_in(const StepArgs& a, int prec, const double* Uin, void* Uout, cudaStream_t s);
+cudaError_t launch_convert_out(const StepArgs& a, int prec, const void* Uin, double* Uout, cudaStream_t s);
+
+// Horizontal means of rho and p of an FP64 full state, one per row of the last axis.
+cudaError_t launch_row_means(const StepArgs& a, const double* U, double* rho_mean, double* p_mean, cudaStream_t s);
+
+// Diagnostics: per-block FP64 partial sums in a fixed order, then one fixed-order reduction.
+enum { DG_MASS = 0, DG_MX, DG_MY, DG_MZ, DG_W, DG_KE, DG_VABS, DG_NSUM };
+enum { DG_UMAX = DG_NSUM, DG_RMIN, DG_PMIN, DG_NAN, DG_NTOT };
+constexpr int DIAG_BLOCKS = 304;
+cudaError_t launch_diagnostics(const StepArgs& a, int prec, const void* U, double* partials, double* out,
+                               cudaStream_t s);
+
+// Step kernel instances (ark_step_*.cu).
+using StepLauncher = cudaError_t (*)(const StepArgs&, dim3 grid, cudaStream_t);
+struct StepKernelInfo {
+    StepLauncher launch;
+    int tx, ty, threads;
+    size_t smem;
+    int blocks_per_sm;
+};
+StepKernelInfo step_kernel_2d(int prec, int visc);
+StepKernelInfo step_kernel_3d(int prec, int visc);
+
+}  // namespace ark

@@ -1,0 +1,87 @@
+// ark_base.h -- FP64 base state of the F32_SPLIT form (host code).
+#pragma once
+
+#include <vector>
+
+#include "ark_common.cuh"
+
+namespace ark {
+
+struct BaseSpec {
+    int nv;              // rows along the gravity axis
+    double lo_v, dv;     // lower coordinate and cell size of that axis
+    double g, gamma, kappa;
+    int bc_lo, bc_hi;    // boundary conditions of that axis
+    double T_lo, T_hi;   // wall temperatures
+};
+
+// FP64 base state of F32_SPLIT: rows -2 .. nv + 1 from the interior row means,
+// ghost rows by the boundary rule of the gravity axis applied to the base,
+// then every table entry formed in FP64 and rounded once.
+inline void build_base_tables(const BaseSpec& s, const std::vector<double>& rho_in, const std::vector<double>& p_in,
+                              std::vector<double>& b64, std::vector<float>& tab)
+{
+    const int nv = s.nv, L = nv + 4;
+    const double dv = s.dv;
+    const double gm1 = s.gamma - 1.0;
+    std::vector<double> rho(L), pr(L), T(L), phi(L);
+    for (int r = -2; r < nv + 2; ++r) phi[r + 2] = -(s.g * (s.lo_v + (r + 0.5) * dv));
+    for (int r = 0; r < nv; ++r) { rho[r + 2] = rho_in[r]; pr[r + 2] = p_in[r]; T[r + 2] = p_in[r] / rho_in[r]; }
+    for (int side = 0; side < 2; ++side) {
+        const int bc = side == 0 ? s.bc_lo : s.bc_hi;
+        const double Tw = side == 0 ? s.T_lo : s.T_hi;
+        for (int layer = 1; layer <= 2; ++layer) {
+            const int g = side == 0 ? -layer : nv - 1 + layer;
+            const int m = side == 0 ? layer - 1 : nv - layer;        // mirror row
+            const int A = layer == 1 ? m : (side == 0 ? -1 : nv);   // inner neighbour
+            if (bc == BC_PERIODIC) {
+                const int w = ((g % nv) + nv) % nv;
+                rho[g + 2] = rho[w + 2]; pr[g + 2] = pr[w + 2]; T[g + 2] = T[w + 2];
+            } else if (bc == BC_OUTFLOW) {
+                const int e = side == 0 ? 0 : nv - 1;
+                rho[g + 2] = rho[e + 2]; pr[g + 2] = pr[e + 2]; T[g + 2] = T[e + 2];
+            } else {
+                const double Tg = bc == BC_REFLECT ? T[m + 2] : 2.0 * Tw - T[m + 2];
+                const double dphi = phi[g + 2] - phi[A + 2];
+                pr[g + 2] = (pr[A + 2] - 0.5 * rho[A + 2] * dphi) / (1.0 + dphi / (2.0 * Tg));
+                rho[g + 2] = pr[g + 2] / Tg;
+                T[g + 2] = Tg;
+            }
+        }
+    }
+    b64.assign(3 * L, 0.0);
+    std::vector<double> W0(L);
+    for (int i = 0; i < L; ++i) {
+        W0[i] = pr[i] / gm1 + rho[i] * phi[i];
+        b64[0 * L + i] = rho[i];
+        b64[1 * L + i] = pr[i];
+        b64[2 * L + i] = W0[i];
+    }
+    std::vector<double> t(NBASE * (size_t)L, 0.0);
+    auto at = [&](int f, int i) -> double& { return t[(size_t)f * L + i]; };
+    for (int i = 0; i < L; ++i) {
+        at(B_RHO0, i) = rho[i];
+        at(B_P0, i) = pr[i];
+        at(B_T0, i) = T[i];
+        at(B_H0, i) = W0[i] + pr[i];
+    }
+    for (int i = 0; i + 1 < L; ++i) {
+        const double S0 = -0.5 * (rho[i] + rho[i + 1]) * (phi[i + 1] - phi[i]);
+        at(B_R0F, i) = (pr[i + 1] - pr[i]) - S0;
+        at(B_DPP, i) = 0.5 * (pr[i + 1] - pr[i]);
+        at(B_DRP, i) = rho[i + 1] - rho[i];
+        at(B_DWP, i) = W0[i + 1] - W0[i];
+    }
+    for (int i = 1; i < L; ++i) {
+        at(B_Q0, i) = 0.5 * (at(B_R0F, i) + at(B_R0F, i - 1));
+        at(B_DPM, i) = 0.5 * (pr[i - 1] - pr[i]);
+        at(B_DRM, i) = rho[i - 1] - rho[i];
+        at(B_DWM, i) = W0[i - 1] - W0[i];
+    }
+    for (int i = 1; i + 1 < L; ++i)
+        at(B_DQ0, i) = s.kappa * ((T[i + 1] - T[i]) - (T[i] - T[i - 1])) / (dv * dv);
+    tab.resize(t.size());
+    for (size_t i = 0; i < t.size(); ++i) tab[i] = (float)t[i];
+}
+
+}  // namespace ark

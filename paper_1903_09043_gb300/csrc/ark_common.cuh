@@ -1,0 +1,60 @@
+// ark_common.cuh -- types shared by the step kernel, the auxiliary kernels and
+// the host side of libark (GB300, sm_103a).
+#pragma once
+
+#include <cstdint>
+
+namespace ark {
+
+enum BC : int { BC_PERIODIC = 0, BC_REFLECT = 1, BC_NOSLIP_T = 2, BC_OUTFLOW = 3 };
+enum Prec : int { P_F64 = 0, P_F32 = 1, P_F32_SPLIT = 2 };
+enum Status : unsigned { ST_NONPHYS = 1u, ST_LTILDE = 2u, ST_NAN = 4u };
+
+// Per-row base-state table (F32_SPLIT only), rows r = -2 .. nv + 1 stored at
+// index r + 2 of each of the NBASE arrays (each nv + 4 long).  Every entry is
+// formed in FP64 on the host and rounded once to the state precision.
+enum BaseField : int {
+    B_RHO0 = 0,  // rho0_r
+    B_P0,        // p0_r
+    B_T0,        // T0_r = p0_r / rho0_r
+    B_H0,        // W0_r + p0_r, W0 = p0/(gamma-1) + rho0 Phi_r
+    B_R0F,       // p0_{r+1} - p0_r - S0_{r+1/2}: base residual of the face above row r
+    B_Q0,        // (R0F_r + R0F_{r-1}) / 2: base part of [Pi*] - S_i in the vertical momentum
+    B_DPP,       // P0_{r+1/2} - p0_r = (p0_{r+1} - p0_r) / 2
+    B_DPM,       // P0_{r-1/2} - p0_r = (p0_{r-1} - p0_r) / 2
+    B_DRP,       // rho0_{r+1} - rho0_r
+    B_DRM,       // rho0_{r-1} - rho0_r
+    B_DWP,       // W0_{r+1} - W0_r
+    B_DWM,       // W0_{r-1} - W0_r
+    B_DQ0,       // kappa [(T0_{r+1} - T0_r) - (T0_r - T0_{r-1})] / dz^2: base heat divergence
+    NBASE
+};
+
+// Everything one step launch needs, passed by value.
+struct StepArgs {
+    int dim;
+    int n[3];               // cells per axis (x, y, z); the last active axis is the gravity axis
+    double dx[3];           // cell sizes
+    double gamma;
+    double g;               // gravity along the last axis: Phi = -g x_last
+    double lo_v;            // lower coordinate of the last axis
+    double mu, kappa, K, cfl;
+    int low_mach;
+    int bc_lo[3], bc_hi[3];
+    double Tw_lo[3], Tw_hi[3];
+    int planes;             // planes of the gravity axis per block
+    int tiles_x, tiles_y;   // in-plane tiles
+    long long ncell;        // cells per field
+    const void* Uin;
+    void* Uout;
+    const void* base;       // BaseField tables (F32_SPLIT), else nullptr
+    const double* base64;   // FP64 rho0, p0, W0 per row, rows -2 .. nv + 1 (F32_SPLIT)
+    double dt_fixed;        // > 0: fixed step; otherwise cfl / smax[slot_read]
+    unsigned long long* smax;  // 3 slots of FP64 bit patterns (max wave rate)
+    int slot_read, slot_write, slot_reset;
+    unsigned int* status;
+    double* time;           // simulated time, advanced by dt each step
+    double* dt_last;        // dt of this step
+};
+
+}  // namespace ark

@@ -1,0 +1,784 @@
+// ark_step.cuh -- the fused explicit step of the all-regime, well-balanced
+// acoustic-transport scheme (arXiv:1903.09043, Sec. 2) for GB300 (sm_103a).
+//
+// One launch = one time step.  Each block owns an in-plane tile of TX x TY
+// cells (TY = 1 in 2D) and marches along the gravity axis (y in 2D, z in 3D)
+// over `planes` planes.  Per plane f it
+//   A  loads U^n of plane f over the tile + 2 ghost cells in-plane (boundary
+//      conditions are applied in the loader; no ghost array exists in HBM) and
+//      forms the primitives (Sec. 3.2 "conservative to primitive");
+//   B  forms the acoustic face values u*, Pi* (theta of Eq. 16) and the
+//      gravity source S of plane f-1's in-plane faces and of the faces
+//      between planes f-1 and f (Sec. 2.1.2);
+//   C  forms L~ and the tilde states of plane f-1 (Sec. 2.1.2) and the
+//      first-order viscous / heat fluxes (Sec. 2.2) around plane f-1;
+//   D  forms the upwind transport fluxes (Sec. 2.1.3) of plane f-2, updates
+//      it, stores U^{n+1} once, and folds its CFL wave rate into a block max.
+// Every conserved field is therefore read from HBM once per step (halo reads
+// hit L2) and written once.  Planes live in small shared-memory rings; values
+// that stay with one output column (z-face fluxes, in-plane viscous sums)
+// live in registers.  Multi-dimensional terms are summed unsplit.
+//
+// Arithmetic forms: F64 (Real = double), F32 (Real = float) and F32_SPLIT
+// (Real = float, the state stores deviations from an FP64 base state per row
+// of the gravity axis; every base-state term, including the well-balanced
+// residual p0_{r+1} - p0_r - S0_{r+1/2}, comes from an FP64 table).
+#pragma once
+
+#include <cuda_runtime.h>
+
+#include "ark_common.cuh"
+
+namespace ark {
+
+template <int DIM, typename Real, bool SPLIT, bool VISC, int TX, int TY>
+struct StepCfg {
+    static constexpr int D = DIM;
+    static constexpr int NF = DIM + 2;
+    static constexpr bool Y = (DIM == 3);
+    static constexpr int HY = Y ? 2 : 0;
+    static constexpr int H1 = Y ? 1 : 0;
+    static constexpr int NT = TX * TY;
+    static constexpr int R2X = TX + 4, R2Y = TY + 2 * HY, NR2 = R2X * R2Y;
+    static constexpr int R1X = TX + 2, R1Y = TY + 2 * H1, NR1 = R1X * R1Y;
+    // x faces bounding R1 cells: left cell lx in [-2, TX], rows ly in [-H1, TY + H1)
+    static constexpr int FXX = TX + 3, NFX = FXX * R1Y;
+    // y faces bounding R1 cells (3D): columns lx in [-1, TX], lower cell ly in [-2, TY]
+    static constexpr int FYY = TY + 3, NFY = Y ? R1X * FYY : 0;
+    // faces of the output cells: x: left lx in [-1, TX - 1]; y: lower ly in [-1, TY - 1]
+    static constexpr int NTX = (TX + 1) * TY;
+    static constexpr int NTY = Y ? TX * (TY + 1) : 0;
+    static constexpr int NVT = D + (VISC ? 1 : 0);   // velocity components (+ temperature)
+    static constexpr int NV = D + 1;                 // dissipative flux components (m_d..., W)
+
+    // shared-memory layout, in units of Real
+    static constexpr int O_VELT = 0;                                   // [3][NVT][NR2]
+    static constexpr int O_FACEF = O_VELT + 3 * NVT * NR2;             // [2][4][NR2] dp, rc, z, rz
+    static constexpr int O_UCONS = O_FACEF + 2 * 4 * NR2;              // [2][NF][NR1]
+    static constexpr int O_ZF = O_UCONS + 2 * NF * NR1;                // [2][3][NR1] u*, dPi*, dS
+    static constexpr int O_XYF = O_ZF + 2 * 3 * NR1;                   // [2][2][NFX + NFY]
+    static constexpr int O_TL = O_XYF + 2 * 2 * (NFX + NFY);           // [2][NF + 1][NR1]
+    static constexpr int O_TFLUX = O_TL + 2 * (NF + 1) * NR1;          // [NF][NTX + NTY]
+    static constexpr int O_VFLUX = O_TFLUX + NF * (NTX + NTY);         // [NV][NTX + NTY]
+    static constexpr int N_REAL = O_VFLUX + (VISC ? NV * (NTX + NTY) : 0);
+    static constexpr size_t SMEM_BYTES = ((N_REAL * sizeof(Real) + 15) / 16) * 16 + NT * sizeof(double);
+
+    __device__ static int i2(int lx, int ly) { return (ly + HY) * R2X + (lx + 2); }
+    __device__ static int i1(int lx, int ly) { return (ly + H1) * R1X + (lx + 1); }
+    __device__ static int ifx(int lx, int ly) { return (ly + H1) * FXX + (lx + 2); }
+    __device__ static int ify(int lx, int ly) { return (ly + 2) * R1X + (lx + 1); }
+    __device__ static int itx(int lx, int ly) { return ly * (TX + 1) + (lx + 1); }
+    __device__ static int ity(int lx, int ly) { return (ly + 1) * TX + lx; }
+};
+
+template <int D, typename Real>
+struct Cell {
+    Real drho, m[D], dW;            // conserved values (deviation form in F32_SPLIT)
+    Real rho, u[D], dp, dT, c;      // full rho, velocity, deviation p and T (full in F64/F32), c
+};
+
+template <typename Real>
+struct Row {
+    Real rho0, p0, T0, phi;
+};
+
+template <typename Real>
+__device__ __forceinline__ Real rcp(Real x) { return Real(1) / x; }
+
+template <typename Real>
+__device__ __forceinline__ Real rsqrt_(Real x);
+template <>
+__device__ __forceinline__ double rsqrt_<double>(double x) { return rsqrt(x); }
+template <>
+__device__ __forceinline__ float rsqrt_<float>(float x) { return rsqrtf(x); }
+
+// Phi at the centre of row r of the gravity axis (Phi = -g x_last).
+__device__ __forceinline__ double phi_row(const StepArgs& a, int r, double dv)
+{
+    return -(a.g * (a.lo_v + (r + 0.5) * dv));
+}
+
+template <typename Real, bool SPLIT>
+__device__ __forceinline__ Row<Real> row_info(const StepArgs& a, int r, int nv, double dv)
+{
+    Row<Real> w;
+    if constexpr (SPLIT) {
+        const Real* B = static_cast<const Real*>(a.base);
+        const int L = nv + 4;
+        w.rho0 = __ldg(B + B_RHO0 * L + r + 2);
+        w.p0 = __ldg(B + B_P0 * L + r + 2);
+        w.T0 = __ldg(B + B_T0 * L + r + 2);
+    } else {
+        w.rho0 = Real(0); w.p0 = Real(0); w.T0 = Real(0);
+    }
+    w.phi = Real(phi_row(a, r, dv));
+    return w;
+}
+
+// Primitive values from conserved values (ideal gas, Sec. 4; p = rho T).
+template <int D, typename Real, bool SPLIT>
+__device__ __forceinline__ void prim(Cell<D, Real>& c, const Row<Real>& w, Real gm1, Real gamma)
+{
+    c.rho = SPLIT ? w.rho0 + c.drho : c.drho;
+    const Real rr = rcp(c.rho);
+    Real ke = Real(0);
+#pragma unroll
+    for (int d = 0; d < D; ++d) {
+        c.u[d] = c.m[d] * rr;
+        ke += c.m[d] * c.u[d];
+    }
+    c.dp = gm1 * (c.dW - Real(0.5) * ke - c.drho * w.phi);
+    const Real p = SPLIT ? w.p0 + c.dp : c.dp;
+    c.dT = SPLIT ? (c.dp - w.T0 * c.drho) * rr : p * rr;
+    c.c = sqrt(gamma * p * rr);
+}
+
+// Conserved values of a ghost built from primitives (rho full, u, dp, dT).
+template <int D, typename Real, bool SPLIT>
+__device__ __forceinline__ void cons_from_prim(Cell<D, Real>& g, const Row<Real>& w, Real gm1, Real gamma)
+{
+    Real ke = Real(0);
+#pragma unroll
+    for (int d = 0; d < D; ++d) {
+        g.m[d] = g.rho * g.u[d];
+        ke += g.rho * g.u[d] * g.u[d];
+    }
+    g.dW = g.dp / gm1 + Real(0.5) * ke + g.drho * w.phi;
+    const Real p = SPLIT ? w.p0 + g.dp : g.dp;
+    g.c = sqrt(gamma * p / g.rho);
+}
+
+// Wall ghost (reflective hydrostatic or no-slip fixed-temperature): velocity
+// mirrored (normal component, or all components, with sign flip);
+// temperature mirrored or reflected about the wall value; pressure from the
+// discrete hydrostatic balance of Eq. 18 with the inner neighbour A, written
+// in deviation form: with base ghost row (rho0_g, T0_g) built by the same rule,
+//   dp_g = (dp_A - dPhi drho_A / 2 + dPhi rho0_g dT_g / (2 T_g)) / (1 + dPhi / (2 T_g)),
+//   drho_g = (dp_g - rho0_g dT_g) / T_g.
+template <int D, typename Real, bool SPLIT>
+__device__ __forceinline__ Cell<D, Real> wall_ghost(const Cell<D, Real>& M, const Cell<D, Real>& A, int bc,
+                                                    int axis, Real Tw, const Row<Real>& wg, Real dphi,
+                                                    Real gm1, Real gamma)
+{
+    Cell<D, Real> g;
+#pragma unroll
+    for (int k = 0; k < D; ++k) g.u[k] = (bc == BC_NOSLIP_T || k == axis) ? -M.u[k] : M.u[k];
+    Real dTg;
+    if (bc == BC_REFLECT) dTg = M.dT;
+    else dTg = SPLIT ? -M.dT : Real(2) * Tw - M.dT;
+    const Real Tg = SPLIT ? wg.T0 + dTg : dTg;
+    Real num = A.dp - Real(0.5) * A.drho * dphi;
+    if constexpr (SPLIT) num += Real(0.5) * wg.rho0 * dphi * dTg / Tg;
+    g.dp = num / (Real(1) + dphi / (Real(2) * Tg));
+    g.drho = SPLIT ? (g.dp - wg.rho0 * dTg) / Tg : g.dp / Tg;
+    g.dT = dTg;
+    g.rho = SPLIT ? wg.rho0 + g.drho : g.drho;
+    cons_from_prim<D, Real, SPLIT>(g, wg, gm1, gamma);
+    return g;
+}
+
+// CFL wave rate of one cell (the time step is cfl / max over cells):
+//   max( sum_d (|u_d| + c) / dx_d , sum_d 2 max(4 mu / (3 rho), kappa (gamma-1) / rho) / dx_d^2 ).
+// b holds the cell's stored values (deviation form in F32_SPLIT); p and rho
+// are returned for the physical checks.
+template <int D, typename Real, bool SPLIT, bool VISC>
+__device__ __forceinline__ Real wave_rate(const Real* b, const Row<Real>& w, Real gm1, Real gamma,
+                                          const Real* invdx, Real mu, Real kappa, Real& p, Real& rho)
+{
+    rho = SPLIT ? w.rho0 + b[0] : b[0];
+    const Real rr = rcp(rho);
+    Real ke = Real(0), sh = Real(0);
+    Real uu[D];
+#pragma unroll
+    for (int d = 0; d < D; ++d) {
+        uu[d] = b[1 + d] * rr;
+        ke += b[1 + d] * uu[d];
+    }
+    const Real dp = gm1 * (b[D + 1] - Real(0.5) * ke - b[0] * w.phi);
+    p = SPLIT ? w.p0 + dp : dp;
+    const Real cs = sqrt(gamma * p * rr);
+#pragma unroll
+    for (int d = 0; d < D; ++d) sh += (fabs(uu[d]) + cs) * invdx[d];
+    if constexpr (VISC) {
+        const Real nu = Real(4.0 / 3.0) * mu * rr, chi = kappa * gm1 * rr;
+        const Real dm = fmax(nu, chi);
+        Real sp = Real(0);
+#pragma unroll
+        for (int d = 0; d < D; ++d) sp += Real(2) * dm * invdx[d] * invdx[d];
+        sh = fmax(sh, sp);
+    }
+    return sh;
+}
+
+template <int DIM, typename Real, bool SPLIT, bool VISC, int TX, int TY>
+struct Stepper {
+    using C = StepCfg<DIM, Real, SPLIT, VISC, TX, TY>;
+    static constexpr int D = DIM;
+    static constexpr int NF = DIM + 2;
+    static constexpr int V = DIM - 1;   // index of the gravity (marching) axis
+
+    const StepArgs& a;
+    const Real* __restrict__ U;
+    long long N;
+    int nx, ny, nv;
+    double dv;
+    Real gm1, gamma;
+
+    __device__ Stepper(const StepArgs& args) : a(args)
+    {
+        U = static_cast<const Real*>(a.Uin);
+        N = a.ncell;
+        nx = a.n[0];
+        ny = D == 3 ? a.n[1] : 1;
+        nv = a.n[V];
+        dv = a.dx[V];
+        gamma = Real(a.gamma);
+        gm1 = Real(a.gamma - 1.0);
+    }
+
+    __device__ Cell<D, Real> load_in(int gx, int gy, int gv, const Row<Real>& w) const
+    {
+        long long idx = D == 3 ? gx + (long long)nx * (gy + (long long)ny * gv) : gx + (long long)nx * gv;
+        Cell<D, Real> c;
+        c.drho = __ldg(U + idx);
+#pragma unroll
+        for (int d = 0; d < D; ++d) c.m[d] = __ldg(U + (1 + d) * N + idx);
+        c.dW = __ldg(U + (D + 1) * N + idx);
+        prim<D, Real, SPLIT>(c, w, gm1, gamma);
+        return c;
+    }
+
+    // in-plane axis rule (axis 0 = x, axis 1 = y in 3D).  All in-plane
+    // ghosts share the row of their plane; dPhi = 0 across in-plane walls.
+    __device__ Cell<D, Real> fetch_x(int gx, int gy, int gv, const Row<Real>& w) const
+    {
+        if (gx >= 0 && gx < nx) return load_in(gx, gy, gv, w);
+        const bool lo = gx < 0;
+        const int bc = lo ? a.bc_lo[0] : a.bc_hi[0];
+        if (bc == BC_PERIODIC) return load_in(((gx % nx) + nx) % nx, gy, gv, w);
+        if (bc == BC_OUTFLOW) return load_in(lo ? 0 : nx - 1, gy, gv, w);
+        const Real Tw = Real(lo ? a.Tw_lo[0] : a.Tw_hi[0]);
+        const Cell<D, Real> M0 = load_in(lo ? 0 : nx - 1, gy, gv, w);
+        Cell<D, Real> g1 = wall_ghost<D, Real, SPLIT>(M0, M0, bc, 0, Tw, w, Real(0), gm1, gamma);
+        const int layer = lo ? -gx : gx - nx + 1;
+        if (layer == 1) return g1;
+        const Cell<D, Real> M1 = load_in(lo ? 1 : nx - 2, gy, gv, w);
+        return wall_ghost<D, Real, SPLIT>(M1, g1, bc, 0, Tw, w, Real(0), gm1, gamma);
+    }
+
+    __device__ Cell<D, Real> fetch_h(int gx, int gy, int gv, const Row<Real>& w) const
+    {
+        if constexpr (D == 3) {
+            if (gy < 0 || gy >= ny) {
+                const bool lo = gy < 0;
+                const int bc = lo ? a.bc_lo[1] : a.bc_hi[1];
+                if (bc == BC_PERIODIC) return fetch_x(gx, ((gy % ny) + ny) % ny, gv, w);
+                if (bc == BC_OUTFLOW) return fetch_x(gx, lo ? 0 : ny - 1, gv, w);
+                const Real Tw = Real(lo ? a.Tw_lo[1] : a.Tw_hi[1]);
+                const Cell<D, Real> M0 = fetch_x(gx, lo ? 0 : ny - 1, gv, w);
+                Cell<D, Real> g1 = wall_ghost<D, Real, SPLIT>(M0, M0, bc, 1, Tw, w, Real(0), gm1, gamma);
+                const int layer = lo ? -gy : gy - ny + 1;
+                if (layer == 1) return g1;
+                const Cell<D, Real> M1 = fetch_x(gx, lo ? 1 : ny - 2, gv, w);
+                return wall_ghost<D, Real, SPLIT>(M1, g1, bc, 1, Tw, w, Real(0), gm1, gamma);
+            }
+        }
+        return fetch_x(gx, gy, gv, w);
+    }
+
+    // full rule: the gravity axis is applied last (x, then y, then the last axis).
+    // Out of line: only cells of ghost planes and of tiles touching the box edge come here.
+    __device__ __noinline__ Cell<D, Real> fetch(int gx, int gy, int gv) const
+    {
+        if (gv >= 0 && gv < nv) return fetch_h(gx, gy, gv, row_info<Real, SPLIT>(a, gv, nv, dv));
+        const bool lo = gv < 0;
+        const int bc = lo ? a.bc_lo[V] : a.bc_hi[V];
+        if (bc == BC_PERIODIC) {
+            const int s = ((gv % nv) + nv) % nv;
+            return fetch_h(gx, gy, s, row_info<Real, SPLIT>(a, s, nv, dv));
+        }
+        const Row<Real> wg = row_info<Real, SPLIT>(a, gv, nv, dv);
+        if (bc == BC_OUTFLOW) {
+            const int s = lo ? 0 : nv - 1;
+            Cell<D, Real> M = fetch_h(gx, gy, s, row_info<Real, SPLIT>(a, s, nv, dv));
+            Cell<D, Real> g = M;   // (rho, u, p) copied; base rows of an outflow ghost copy the edge row
+            cons_from_prim<D, Real, SPLIT>(g, wg, gm1, gamma);
+            return g;
+        }
+        const Real Tw = Real(lo ? a.Tw_lo[V] : a.Tw_hi[V]);
+        const int r0 = lo ? 0 : nv - 1, r1 = lo ? 1 : nv - 2, g1r = lo ? -1 : nv;
+        const Row<Real> w0 = row_info<Real, SPLIT>(a, r0, nv, dv);
+        const Row<Real> w1g = row_info<Real, SPLIT>(a, g1r, nv, dv);
+        const Cell<D, Real> M0 = fetch_h(gx, gy, r0, w0);
+        const Real dphi1 = Real(phi_row(a, g1r, dv) - phi_row(a, r0, dv));
+        Cell<D, Real> g1 = wall_ghost<D, Real, SPLIT>(M0, M0, bc, V, Tw, w1g, dphi1, gm1, gamma);
+        if (gv == g1r) return g1;
+        const Row<Real> w1 = row_info<Real, SPLIT>(a, r1, nv, dv);
+        const Cell<D, Real> M1 = fetch_h(gx, gy, r1, w1);
+        const Real dphi2 = Real(phi_row(a, gv, dv) - phi_row(a, g1r, dv));
+        return wall_ghost<D, Real, SPLIT>(M1, g1, bc, V, Tw, wg, dphi2, gm1, gamma);
+    }
+};
+
+// Acoustic face values of Sec. 2.1.2 with the low-Mach correction (Eq. 16):
+//   a = K max(z_L, z_R), z = rho c;  u* = (u_L + u_R)/2 - (p_R - p_L - S)/(2a);
+//   theta = min(|u*| / max(c_L, c_R), 1);  Pi* = (p_L + p_R)/2 - a theta (u_R - u_L)/2.
+// Deviation form: pjump = (base residual) + dp_R - dp_L - dS, dPi* excludes the
+// base face pressure (p0_L + p0_R)/2.  1/(2a) and 1/max(c) use per-cell reciprocals.
+template <typename Real>
+__device__ __forceinline__ void acoustic_face(Real uL, Real uR, Real dpL, Real dpR, Real zL, Real zR, Real rzL,
+                                              Real rzR, Real rcL, Real rcR, Real pjump_base, Real dS, Real K,
+                                              Real halfInvK, int low_mach, Real& ustar, Real& dPi)
+{
+    const Real a = K * fmax(zL, zR);
+    const Real inv2a = halfInvK * fmin(rzL, rzR);
+    ustar = Real(0.5) * (uL + uR) - (pjump_base + dpR - dpL - dS) * inv2a;
+    Real theta = Real(1);
+    if (low_mach) theta = fmin(fabs(ustar) * fmin(rcL, rcR), Real(1));
+    dPi = Real(0.5) * (dpL + dpR) - Real(0.5) * a * theta * (uR - uL);
+}
+
+template <int DIM, typename Real, bool SPLIT, bool VISC, int TX, int TY>
+__global__ void __launch_bounds__(TX * TY, sizeof(Real) == 8 ? 1 : 2)
+ark_step_kernel(const StepArgs a)
+{
+    using C = StepCfg<DIM, Real, SPLIT, VISC, TX, TY>;
+    constexpr int D = DIM, NF = DIM + 2, V = DIM - 1;
+    constexpr int NT = C::NT, NR1 = C::NR1, NR2 = C::NR2;
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    Real* sm = reinterpret_cast<Real*>(smem_raw);
+    double* red = reinterpret_cast<double*>(smem_raw + ((C::N_REAL * sizeof(Real) + 15) / 16) * 16);
+
+    Stepper<DIM, Real, SPLIT, VISC, TX, TY> S(a);
+    const int tid = threadIdx.x;
+    const int tile = blockIdx.x;
+    const int x0 = (tile % a.tiles_x) * TX;
+    const int y0 = D == 3 ? (tile / a.tiles_x) * TY : 0;
+    const int z0 = blockIdx.y * a.planes;
+    const int z1 = min(z0 + a.planes, S.nv);
+    const int nx = S.nx, ny = S.ny;
+
+    // time step of this step (identical in every block)
+    double dt_d = a.dt_fixed;
+    if (!(dt_d > 0.0)) dt_d = a.cfl / __longlong_as_double((long long)a.smax[a.slot_read]);
+    if (blockIdx.x == 0 && blockIdx.y == 0 && tid == 0) {
+        a.smax[a.slot_reset] = 0ull;
+        *a.time += dt_d;
+        *a.dt_last = dt_d;
+    }
+    Real lam[3], dtdx[3];
+#pragma unroll
+    for (int d = 0; d < 3; ++d) {
+        lam[d] = d < D ? Real(dt_d / a.dx[d]) : Real(0);
+        dtdx[d] = lam[d];
+    }
+    const Real dt = Real(dt_d);
+    const Real K = Real(a.K), halfInvK = Real(0.5 / a.K);
+    const Real mu = Real(a.mu), kappa = Real(a.kappa), eta = Real(-2.0 / 3.0 * a.mu);
+    const Real invdx[3] = {Real(1.0 / a.dx[0]), Real(1.0 / a.dx[1]), Real(1.0 / a.dx[2])};
+    const Real* __restrict__ Bt = static_cast<const Real*>(a.base);
+    const int BL = S.nv + 4;
+
+    // this thread's output cell
+    const int olx = tid % TX, oly = tid / TX;
+    const int ogx = x0 + olx, ogy = y0 + oly;
+    const bool ocol = ogx < nx && (D == 2 || ogy < ny);
+
+    // register carries along the column
+    Real zt_lo[NF];            // transport flux through the lower z face of the output plane
+    Real us_lo = Real(0);      // u* there
+    Real zvA[C::NV], zvB[C::NV], dxy_prev[C::NV];
+#pragma unroll
+    for (int q = 0; q < NF; ++q) zt_lo[q] = Real(0);
+#pragma unroll
+    for (int q = 0; q < C::NV; ++q) { zvA[q] = zvB[q] = dxy_prev[q] = Real(0); }
+    Real smax_t = Real(0);
+    unsigned status = 0u;
+
+    auto velT = [&](int plane, int comp, int idx) -> Real& {
+        const int s = ((plane % 3) + 3) % 3;
+        return sm[C::O_VELT + (s * C::NVT + comp) * NR2 + idx];
+    };
+    auto facef = [&](int plane, int comp, int idx) -> Real& {
+        return sm[C::O_FACEF + ((plane & 1) * 4 + comp) * NR2 + idx];
+    };
+    auto ucons = [&](int plane, int comp, int idx) -> Real& {
+        return sm[C::O_UCONS + ((plane & 1) * NF + comp) * NR1 + idx];
+    };
+    // z face between planes q and q+1 is stored in slot (q + 1) & 1
+    auto zf = [&](int upper, int comp, int idx) -> Real& {
+        return sm[C::O_ZF + ((upper & 1) * 3 + comp) * NR1 + idx];
+    };
+    auto xyf = [&](int plane, int dir, int comp, int idx) -> Real& {
+        const int base = C::O_XYF + (plane & 1) * 2 * (C::NFX + C::NFY);
+        return sm[base + comp * (C::NFX + C::NFY) + (dir ? C::NFX : 0) + idx];
+    };
+    auto tl = [&](int plane, int comp, int idx) -> Real& {
+        return sm[C::O_TL + ((plane & 1) * (NF + 1) + comp) * NR1 + idx];
+    };
+    auto tflux = [&](int dir, int comp, int idx) -> Real& {
+        return sm[C::O_TFLUX + comp * (C::NTX + C::NTY) + (dir ? C::NTX : 0) + idx];
+    };
+    auto vflux = [&](int dir, int comp, int idx) -> Real& {
+        return sm[C::O_VFLUX + comp * (C::NTX + C::NTY) + (dir ? C::NTX : 0) + idx];
+    };
+    auto base = [&](int field, int r) -> Real { return SPLIT ? __ldg(Bt + field * BL + r + 2) : Real(0); };
+
+    for (int f = z0 - 2; f <= z1 + 1; ++f) {
+        // ---------------- A: load plane f, primitives ----------------
+        const bool fin = f >= 0 && f < S.nv;
+        const Row<Real> wf = row_info<Real, SPLIT>(a, fin ? f : 0, S.nv, S.dv);
+        for (int c = tid; c < NR2; c += NT) {
+            const int lx = c % C::R2X - 2, ly = c / C::R2X - C::HY;
+            int gx = x0 + lx, gy = y0 + ly;
+            gx = min(max(gx, -2), nx + 1);
+            if (D == 3) gy = min(max(gy, -2), ny + 1);
+            Cell<D, Real> cell;
+            if (fin && gx >= 0 && gx < nx && (D == 2 || (gy >= 0 && gy < ny))) cell = S.load_in(gx, gy, f, wf);
+            else cell = S.fetch(gx, gy, f);
+#pragma unroll
+            for (int d = 0; d < D; ++d) velT(f, d, c) = cell.u[d];
+            if constexpr (VISC) velT(f, D, c) = cell.dT;
+            const Real rc = rcp(cell.c);
+            facef(f, 0, c) = cell.dp;
+            facef(f, 1, c) = rc;
+            facef(f, 2, c) = cell.rho * cell.c;
+            facef(f, 3, c) = rc * rcp(cell.rho);
+            if (lx >= -1 && lx <= TX && ly >= -C::H1 && ly < TY + C::H1) {
+                const int c1 = C::i1(lx, ly);
+                ucons(f, 0, c1) = cell.drho;
+#pragma unroll
+                for (int d = 0; d < D; ++d) ucons(f, 1 + d, c1) = cell.m[d];
+                ucons(f, D + 1, c1) = cell.dW;
+            }
+        }
+        __syncthreads();
+
+        // ---------------- B: acoustic faces ----------------
+        const int q1 = f - 1;   // plane of the in-plane faces and of the tilde states
+        if (f >= z0) {
+            // in-plane x faces of plane f-1 bounding R1 cells
+            for (int e = tid; e < C::NFX; e += NT) {
+                const int lx = e % C::FXX - 2, ly = e / C::FXX - C::H1;
+                const int iL = C::i2(lx, ly), iR = C::i2(lx + 1, ly);
+                Real us, dPi;
+                acoustic_face<Real>(velT(q1, 0, iL), velT(q1, 0, iR), facef(q1, 0, iL), facef(q1, 0, iR),
+                                    facef(q1, 2, iL), facef(q1, 2, iR), facef(q1, 3, iL), facef(q1, 3, iR),
+                                    facef(q1, 1, iL), facef(q1, 1, iR), Real(0), Real(0), K, halfInvK,
+                                    a.low_mach, us, dPi);
+                xyf(q1, 0, 0, e) = us;
+                xyf(q1, 0, 1, e) = dPi;
+            }
+            if constexpr (D == 3) {
+                for (int e = tid; e < C::NFY; e += NT) {
+                    const int lx = e % C::R1X - 1, ly = e / C::R1X - 2;
+                    const int iL = C::i2(lx, ly), iR = C::i2(lx, ly + 1);
+                    Real us, dPi;
+                    acoustic_face<Real>(velT(q1, 1, iL), velT(q1, 1, iR), facef(q1, 0, iL), facef(q1, 0, iR),
+                                        facef(q1, 2, iL), facef(q1, 2, iR), facef(q1, 3, iL), facef(q1, 3, iR),
+                                        facef(q1, 1, iL), facef(q1, 1, iR), Real(0), Real(0), K, halfInvK,
+                                        a.low_mach, us, dPi);
+                    xyf(q1, 1, 0, e) = us;
+                    xyf(q1, 1, 1, e) = dPi;
+                }
+            }
+        }
+        if (f >= z0 - 1) {
+            // faces between planes f-1 (low side) and f (high side), over R1 cells
+            const Real dphi = Real(phi_row(a, f, S.dv) - phi_row(a, f - 1, S.dv));
+            const Real r0f = base(B_R0F, f - 1);
+            for (int c = tid; c < NR1; c += NT) {
+                const int lx = c % C::R1X - 1, ly = c / C::R1X - C::H1;
+                const int i = C::i2(lx, ly);
+                const Real dS = Real(-0.5) * (ucons(q1, 0, c) + ucons(f, 0, c)) * dphi;
+                Real us, dPi;
+                acoustic_face<Real>(velT(q1, V, i), velT(f, V, i), facef(q1, 0, i), facef(f, 0, i),
+                                    facef(q1, 2, i), facef(f, 2, i), facef(q1, 3, i), facef(f, 3, i),
+                                    facef(q1, 1, i), facef(f, 1, i), r0f, dS, K, halfInvK, a.low_mach, us, dPi);
+                zf(f, 0, c) = us;
+                zf(f, 1, c) = dPi;
+                zf(f, 2, c) = dS;
+            }
+        }
+        __syncthreads();
+
+        // ---------------- C: tilde states of plane f-1; dissipative fluxes ----------------
+        if (f >= z0) {
+            const Real rho0 = base(B_RHO0, q1), H0 = base(B_H0, q1), Q0 = base(B_Q0, q1);
+            const Real dPp = base(B_DPP, q1), dPm = base(B_DPM, q1);
+            for (int c = tid; c < NR1; c += NT) {
+                const int lx = c % C::R1X - 1, ly = c / C::R1X - C::H1;
+                // in-plane face indices
+                const int exp_ = C::ifx(lx, ly), exm = C::ifx(lx - 1, ly);
+                Real usx_p = xyf(q1, 0, 0, exp_), usx_m = xyf(q1, 0, 0, exm);
+                Real pix_p = xyf(q1, 0, 1, exp_), pix_m = xyf(q1, 0, 1, exm);
+                const Real usz_p = zf(f, 0, c), usz_m = zf(q1, 0, c);
+                const Real piz_p = zf(f, 1, c), piz_m = zf(q1, 1, c);
+                const Real dSz_p = zf(f, 2, c), dSz_m = zf(q1, 2, c);
+                Real ell = lam[0] * (usx_p - usx_m);
+                Real m_t[D];
+                m_t[0] = ucons(q1, 1, c) - lam[0] * (pix_p - pix_m);
+                Real W_t = ucons(q1, D + 1, c) - lam[0] * (pix_p * usx_p - pix_m * usx_m);
+                if constexpr (D == 3) {
+                    const int eyp = C::ify(lx, ly), eym = C::ify(lx, ly - 1);
+                    const Real usy_p = xyf(q1, 1, 0, eyp), usy_m = xyf(q1, 1, 0, eym);
+                    const Real piy_p = xyf(q1, 1, 1, eyp), piy_m = xyf(q1, 1, 1, eym);
+                    ell += lam[1] * (usy_p - usy_m);
+                    m_t[1] = ucons(q1, 2, c) - lam[1] * (piy_p - piy_m);
+                    W_t -= lam[1] * (piy_p * usy_p - piy_m * usy_m);
+                }
+                ell += lam[V] * (usz_p - usz_m);
+                m_t[V] = ucons(q1, 1 + V, c) - lam[V] * (piz_p - piz_m) + lam[V] * Real(0.5) * (dSz_p + dSz_m);
+                if constexpr (SPLIT) m_t[V] -= lam[V] * Q0;
+                W_t -= lam[V] * (piz_p * usz_p - piz_m * usz_m);
+                if constexpr (SPLIT) W_t -= lam[V] * (dPp * usz_p - dPm * usz_m) + H0 * ell;
+                const Real L = Real(1) + ell;
+                const Real rL = rcp(L);
+                Real rho_t = SPLIT ? (ucons(q1, 0, c) - rho0 * ell) * rL : ucons(q1, 0, c) * rL;
+                tl(q1, 0, c) = rho_t;
+#pragma unroll
+                for (int d = 0; d < D; ++d) tl(q1, 1 + d, c) = m_t[d] * rL;
+                tl(q1, D + 1, c) = W_t * rL;
+                tl(q1, NF, c) = L;
+                const bool valid = (x0 + lx) >= 0 && (x0 + lx) < nx && (D == 2 || ((y0 + ly) >= 0 && (y0 + ly) < ny)) &&
+                                   q1 >= 0 && q1 < S.nv;
+                if (valid && !(L > Real(0))) status |= ST_LTILDE;
+            }
+        }
+        if constexpr (VISC) {
+            // dissipative fluxes (Sec. 2.2) from U^n: in-plane faces of plane f-1's output cells,
+            // with tangential derivatives averaged over the two cells of the face
+            if (f >= z0 + 1 && f <= z1) {
+                const int qm = f - 2, q0 = f - 1, qp = f;
+                for (int e = tid; e < C::NTX + C::NTY; e += NT) {
+                    const int dir = e < C::NTX ? 0 : 1;
+                    int lxL, lyL, lxR, lyR;
+                    if (dir == 0) {
+                        lxL = e % (TX + 1) - 1; lyL = e / (TX + 1); lxR = lxL + 1; lyR = lyL;
+                    } else {
+                        const int e2 = e - C::NTX;
+                        lxL = e2 % TX; lyL = e2 / TX - 1; lxR = lxL; lyR = lyL + 1;
+                    }
+                    const int iL = C::i2(lxL, lyL), iR = C::i2(lxR, lyR);
+                    Real grad[3][3];   // grad[a][q] = d u_q / d x_a at the face
+#pragma unroll
+                    for (int aa = 0; aa < 3; ++aa)
+#pragma unroll
+                        for (int q = 0; q < 3; ++q) grad[aa][q] = Real(0);
+                    const Real ind = invdx[dir];
+#pragma unroll
+                    for (int q = 0; q < D; ++q) grad[dir][q] = (velT(q0, q, iR) - velT(q0, q, iL)) * ind;
+                    // tangential in-plane direction (3D only)
+                    if constexpr (D == 3) {
+                        const int t = 1 - dir;
+                        const int sx = t == 0 ? 1 : 0, sy = t == 1 ? 1 : 0;
+                        const int Lp = C::i2(lxL + sx, lyL + sy), Lm = C::i2(lxL - sx, lyL - sy);
+                        const int Rp = C::i2(lxR + sx, lyR + sy), Rm = C::i2(lxR - sx, lyR - sy);
+#pragma unroll
+                        for (int q = 0; q < D; ++q)
+                            grad[t][q] = Real(0.25) *
+                                         ((velT(q0, q, Lp) - velT(q0, q, Lm)) + (velT(q0, q, Rp) - velT(q0, q, Rm))) *
+                                         invdx[t];
+                    }
+                    // tangential along the gravity axis: planes f and f-2
+#pragma unroll
+                    for (int q = 0; q < D; ++q)
+                        grad[V][q] = Real(0.25) *
+                                     ((velT(qp, q, iL) - velT(qm, q, iL)) + (velT(qp, q, iR) - velT(qm, q, iR))) *
+                                     invdx[V];
+                    Real divu = Real(0);
+#pragma unroll
+                    for (int aa = 0; aa < D; ++aa) divu += grad[aa][aa];
+                    Real work = Real(0);
+#pragma unroll
+                    for (int q = 0; q < D; ++q) {
+                        Real tau = mu * (grad[dir][q] + grad[q][dir]);
+                        if (q == dir) tau += eta * divu;
+                        work += tau * Real(0.5) * (velT(q0, q, iL) + velT(q0, q, iR));
+                        vflux(dir, q, dir ? e - C::NTX : e) = tau;
+                    }
+                    const Real heat = kappa * (velT(q0, D, iR) - velT(q0, D, iL)) * ind;
+                    vflux(dir, D, dir ? e - C::NTX : e) = work + heat;
+                }
+            }
+        }
+        // z-face (f-1, f) dissipative flux of this thread's column
+        Real zv_new[C::NV];
+#pragma unroll
+        for (int q = 0; q < C::NV; ++q) zv_new[q] = Real(0);
+        if constexpr (VISC) {
+            if (f >= z0 && f <= z1) {
+                const int iL = C::i2(olx, oly);
+                const int q0 = f - 1, qp = f;
+                Real grad[3][3];
+#pragma unroll
+                for (int aa = 0; aa < 3; ++aa)
+#pragma unroll
+                    for (int q = 0; q < 3; ++q) grad[aa][q] = Real(0);
+#pragma unroll
+                for (int q = 0; q < D; ++q) grad[V][q] = (velT(qp, q, iL) - velT(q0, q, iL)) * invdx[V];
+#pragma unroll
+                for (int t = 0; t < D - 1; ++t) {
+                    const int sx = t == 0 ? 1 : 0, sy = t == 1 ? 1 : 0;
+                    const int Pp = C::i2(olx + sx, oly + sy), Pm = C::i2(olx - sx, oly - sy);
+#pragma unroll
+                    for (int q = 0; q < D; ++q)
+                        grad[t][q] = Real(0.25) *
+                                     ((velT(q0, q, Pp) - velT(q0, q, Pm)) + (velT(qp, q, Pp) - velT(qp, q, Pm))) *
+                                     invdx[t];
+                }
+                Real divu = Real(0);
+#pragma unroll
+                for (int aa = 0; aa < D; ++aa) divu += grad[aa][aa];
+                Real work = Real(0);
+#pragma unroll
+                for (int q = 0; q < D; ++q) {
+                    Real tau = mu * (grad[V][q] + grad[q][V]);
+                    if (q == V) tau += eta * divu;
+                    work += tau * Real(0.5) * (velT(q0, q, iL) + velT(qp, q, iL));
+                    zv_new[q] = tau;
+                }
+                zv_new[D] = work + kappa * (velT(qp, D, iL) - velT(q0, D, iL)) * invdx[V];
+            }
+        }
+        __syncthreads();
+
+        // ---------------- D: transport fluxes, update of plane f-2 ----------------
+        const int q = f - 2;
+        Real dxy_new[C::NV];
+#pragma unroll
+        for (int k = 0; k < C::NV; ++k) dxy_new[k] = Real(0);
+        if constexpr (VISC) {
+            if (f >= z0 + 1 && f <= z1) {
+                // in-plane viscous divergence of plane f-1 for this column
+#pragma unroll
+                for (int k = 0; k < C::NV; ++k)
+                    dxy_new[k] = (vflux(0, k, C::itx(olx, oly)) - vflux(0, k, C::itx(olx - 1, oly))) * dtdx[0];
+                if constexpr (D == 3) {
+#pragma unroll
+                    for (int k = 0; k < C::NV; ++k)
+                        dxy_new[k] += (vflux(1, k, C::ity(olx, oly)) - vflux(1, k, C::ity(olx, oly - 1))) * dtdx[1];
+                }
+            }
+        }
+        if (f >= z0 + 2) {
+            // upwind transport fluxes through the in-plane faces of the output cells
+            for (int e = tid; e < C::NTX + C::NTY; e += NT) {
+                const int dir = e < C::NTX ? 0 : 1;
+                int lxL, lyL, lxR, lyR, fe;
+                if (dir == 0) {
+                    lxL = e % (TX + 1) - 1; lyL = e / (TX + 1); lxR = lxL + 1; lyR = lyL;
+                    fe = C::ifx(lxL, lyL);
+                } else {
+                    const int e2 = e - C::NTX;
+                    lxL = e2 % TX; lyL = e2 / TX - 1; lxR = lxL; lyR = lyL + 1;
+                    fe = C::ify(lxL, lyL);
+                }
+                const Real us = xyf(q, dir, 0, fe);
+                const int up = us >= Real(0) ? C::i1(lxL, lyL) : C::i1(lxR, lyR);
+                const int te = dir ? e - C::NTX : e;
+#pragma unroll
+                for (int k = 0; k < NF; ++k) tflux(dir, k, te) = tl(q, k, up) * us;
+            }
+        }
+        Real zt_hi[NF];
+        Real us_hi = Real(0);
+#pragma unroll
+        for (int k = 0; k < NF; ++k) zt_hi[k] = Real(0);
+        if (f >= z0 + 1) {
+            // transport flux through the face between planes f-2 and f-1 of this column
+            const int c1 = C::i1(olx, oly);
+            us_hi = zf(f - 1, 0, c1);
+            const int src = us_hi >= Real(0) ? (f - 2) : (f - 1);
+#pragma unroll
+            for (int k = 0; k < NF; ++k) zt_hi[k] = tl(src, k, c1) * us_hi;
+            if constexpr (SPLIT) {
+                // base-state part of the upwind value relative to the row below (plane f-2)
+                if (!(us_hi >= Real(0))) {
+                    zt_hi[0] += base(B_DRP, f - 2) * us_hi;
+                    zt_hi[D + 1] += base(B_DWP, f - 2) * us_hi;
+                }
+            }
+        }
+        __syncthreads();
+        if (f >= z0 + 2) {
+            const int c1 = C::i1(olx, oly);
+            const Real L = tl(q, NF, c1);
+            Real nb[NF];
+#pragma unroll
+            for (int k = 0; k < NF; ++k) {
+                Real acc = tl(q, k, c1) * L;
+                acc -= lam[0] * (tflux(0, k, C::itx(olx, oly)) - tflux(0, k, C::itx(olx - 1, oly)));
+                if constexpr (D == 3)
+                    acc -= lam[1] * (tflux(1, k, C::ity(olx, oly)) - tflux(1, k, C::ity(olx, oly - 1)));
+                nb[k] = acc;
+            }
+            // flux through the upper z face uses the base of row q; the lower face
+            // flux (computed relative to row q-1) is shifted to row q's base
+            Real lowfix[NF];
+#pragma unroll
+            for (int k = 0; k < NF; ++k) lowfix[k] = zt_lo[k];
+            if constexpr (SPLIT) {
+                // lower face, upwind from below (row q-1): value relative to row q
+                // is b~ + (b0_{q-1} - b0_q); from above it is already relative to row q
+                if (us_lo >= Real(0)) {
+                    lowfix[0] += base(B_DRM, q) * us_lo;
+                    lowfix[D + 1] += base(B_DWM, q) * us_lo;
+                } else {
+                    // the carried flux was shifted to row q-1 by B_DRP of row q-1; undo it
+                    lowfix[0] -= base(B_DRP, q - 1) * us_lo;
+                    lowfix[D + 1] -= base(B_DWP, q - 1) * us_lo;
+                }
+            }
+#pragma unroll
+            for (int k = 0; k < NF; ++k) nb[k] -= lam[V] * (zt_hi[k] - lowfix[k]);
+            if constexpr (VISC) {
+#pragma unroll
+                for (int k = 0; k < C::NV; ++k) {
+                    const Real dv_ = dxy_prev[k] + (zvB[k] - zvA[k]) * dtdx[V];
+                    nb[1 + k] += dv_;   // k < D: momentum m_k, k == D: energy (index D + 1)
+                }
+                if constexpr (SPLIT) nb[D + 1] += dt * base(B_DQ0, q);
+            }
+            // store U^{n+1}
+            if (ocol) {
+                Real* Uo = static_cast<Real*>(a.Uout);
+                const long long idx = D == 3 ? ogx + (long long)nx * (ogy + (long long)ny * q)
+                                             : ogx + (long long)nx * q;
+#pragma unroll
+                for (int k = 0; k < NF; ++k) Uo[k * S.N + idx] = nb[k];
+                // CFL wave rate of U^{n+1} (next step's dt) and physical checks
+                const Row<Real> w = row_info<Real, SPLIT>(a, q, S.nv, S.dv);
+                Real p, rho;
+                const Real sh = wave_rate<D, Real, SPLIT, VISC>(nb, w, S.gm1, S.gamma, invdx, mu, kappa, p, rho);
+                if (!(sh <= smax_t)) smax_t = (sh == sh) ? sh : smax_t;
+                if (sh != sh || p != p) status |= ST_NAN;
+                if (!(rho > Real(0)) || !(p > Real(0))) status |= ST_NONPHYS;
+            }
+        }
+        // rotate the column carries
+        if (f >= z0 + 1) {
+#pragma unroll
+            for (int k = 0; k < NF; ++k) zt_lo[k] = zt_hi[k];
+            us_lo = us_hi;
+        }
+#pragma unroll
+        for (int k = 0; k < C::NV; ++k) {
+            zvA[k] = zvB[k];
+            zvB[k] = zv_new[k];
+            dxy_prev[k] = dxy_new[k];
+        }
+    }
+
+    // block max of the wave rate -> one atomic per block
+    red[tid] = double(smax_t);
+    __syncthreads();
+    for (int s = NT / 2; s > 0; s >>= 1) {
+        if (tid < s) red[tid] = fmax(red[tid], red[tid + s]);
+        __syncthreads();
+    }
+    if (tid == 0) atomicMax(a.smax + a.slot_write, (unsigned long long)__double_as_longlong(red[0]));
+    if (status) atomicOr(a.status, status);
+}
+
+}  // namespace ark

@@ -1,0 +1,79 @@
+"""The C-ABI library: it loads, exports every entry point include/ark.h
+declares, and rejects invalid parameters before touching a device (so these
+run without a GPU)."""
+import ctypes
+import os
+import re
+
+import pytest
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+HEADER = os.path.join(ROOT, "include", "ark.h")
+
+
+def _declared():
+    text = open(HEADER).read()
+    text = re.sub(r"/\*.*?\*/", "", text, flags=re.S)
+    return sorted(set(re.findall(r"\b(ark_[a-z_0-9]+)\s*\(", text)))
+
+
+@pytest.fixture(scope="module")
+def ark():
+    from paper_1903_09043_gb300 import build
+    build.build()
+    from paper_1903_09043_gb300 import ark as mod
+    return mod
+
+
+def test_library_exports_every_declared_symbol(ark):
+    lib = ctypes.CDLL(ark.LIB_PATH)
+    names = _declared()
+    assert len(names) >= 12
+    for name in names:
+        assert hasattr(lib, name), name
+        assert hasattr(ark, name), f"binding lacks {name}"
+
+
+def test_status_strings(ark):
+    for code in range(7):
+        assert ark.ark_status_string(code)
+    assert ark.ark_status_string(0) == b"ok"
+
+
+def _params(ark, **kw):
+    from paper_1903_09043_gb300 import inputs as I
+    prob, _ = I.rayleigh_benard(2, (16, 8), amp=0.0)
+    prob = prob.replace(**{k: v for k, v in kw.items() if k in prob.__dataclass_fields__})
+    return ark.params_from_problem(prob, kw.get("precision", ark.ARK_F64))
+
+
+@pytest.mark.parametrize("mutate,status", [
+    (lambda p: setattr(p.grid, "dim", 4), 1),
+    (lambda p: setattr(p.eos, "gamma", 1.0), 1),
+    (lambda p: setattr(p, "K", 0.5), 1),
+    (lambda p: setattr(p, "cfl", 0.0), 1),
+    (lambda p: setattr(p, "mu", -1.0), 1),
+    (lambda p: setattr(p, "low_mach", 3), 1),
+    (lambda p: setattr(p, "precision", 7), 1),
+    (lambda p: p.bc.lo.__setitem__(0, 9), 1),
+    (lambda p: p.bc.lo.__setitem__(0, 1), 1),                       # periodic pair broken
+    (lambda p: (p.bc.lo.__setitem__(1, 0), p.bc.hi.__setitem__(1, 0)), 1),   # gravity along periodic axis
+    (lambda p: p.grid.n.__setitem__(1, 1), 1),                       # wall axis with one cell
+    (lambda p: p.bc.T_lo.__setitem__(1, 0.0), 1),                    # non-positive wall temperature
+    (lambda p: (setattr(p, "precision", 2), p.bc.lo.__setitem__(0, 2), p.bc.hi.__setitem__(0, 2),
+                p.bc.T_lo.__setitem__(0, 1.0), p.bc.T_hi.__setitem__(0, 1.0)), 5),
+])
+def test_invalid_parameters_rejected_before_device_work(ark, mutate, status):
+    p = _params(ark)
+    mutate(p)
+    h = ark._H()
+    st = ark.ark_create(ctypes.byref(p), None, ctypes.byref(h))
+    assert st == status
+    assert not h.value
+
+
+def test_null_arguments(ark):
+    assert ark.ark_create(None, None, None) == ark.ARK_ERR_INVALID_ARG
+    assert ark.ark_destroy(None) == ark.ARK_ERR_INVALID_ARG
+    assert ark.ark_step(None, 1, -1.0) == ark.ARK_ERR_INVALID_ARG
+    assert ark.ark_last_error(None) == b"null handle"

@@ -1,0 +1,264 @@
+"""CUDA step (through the C ABI) against the FP64 CPU oracle, element by element.
+
+Sizes span several tiles and ragged tails (2D tiles are 256 cells wide and
+march along y; 3D tiles are 16 x 16 and march along z), every boundary
+condition, with and without dissipation, with the low-Mach correction on and
+off; plus configurations of the paper's workloads at their full sizes.
+"""
+import numpy as np
+import pytest
+
+import oracle as O
+from paper_1903_09043_gb300 import inputs as I
+from parity import F32_STEP_TOL, F64_TOL, field_errors, max_error
+
+pytestmark = pytest.mark.gpu
+
+O.set_threads(1)
+
+
+def _ark():
+    from paper_1903_09043_gb300 import ark
+    return ark
+
+
+def _stream():
+    import torch
+    return torch.cuda.current_stream().cuda_stream
+
+
+def gpu_run(prob, U, nsteps, precision="f64", dt=-1.0):
+    ark = _ark()
+    with ark.Solver(prob, precision, stream=_stream()) as s:
+        s.set_state(U)
+        s.step(nsteps, dt)
+        V = s.get_state()
+        d = s.diagnostics(check=False)
+    return V, d
+
+
+CASES = {
+    "2d_periodic": lambda: I.random_periodic(2, (20, 13), seed=1),
+    "2d_periodic_visc": lambda: I.random_periodic(2, (20, 13), seed=2, mu=0.02, kappa=0.03),
+    "2d_periodic_visc_theta1": lambda: I.random_periodic(2, (23, 9), seed=3, mu=0.02, kappa=0.03, low_mach=0),
+    "2d_atmosphere_ragged": lambda: I.atmosphere((37, 29)),
+    "2d_atmosphere_theta1": lambda: I.atmosphere((37, 29), low_mach=0),
+    "2d_strat_noslip_visc": lambda: I.stratified_random(2, (17, 11), mu=0.01, kappa=0.02),
+    "2d_strat_reflect": lambda: I.stratified_random(2, (9, 14), walls=I.REFLECT_HYDRO),
+    "2d_two_tiles_ragged": lambda: I.random_periodic(2, (300, 6), seed=5, mu=0.01, kappa=0.01),
+    "2d_three_tiles": lambda: I.stratified_random(2, (530, 7), mu=0.01, kappa=0.01),
+    "2d_sod_x_outflow": lambda: I.sod(64, axis=0),
+    "2d_sod_y_outflow": lambda: I.sod(64, axis=1),
+    "2d_column_nx1": lambda: I.well_balanced_column(40),
+    "2d_walls_n2": lambda: I.stratified_random(2, (5, 2), mu=0.01, kappa=0.01),
+    "3d_periodic_visc": lambda: I.random_periodic(3, (9, 7, 11), seed=3, mu=0.02, kappa=0.03),
+    "3d_strat_noslip_visc_ragged": lambda: I.stratified_random(3, (7, 18, 9), mu=0.01, kappa=0.02),
+    "3d_strat_reflect": lambda: I.stratified_random(3, (19, 6, 8), walls=I.REFLECT_HYDRO),
+    "3d_multi_tile": lambda: I.stratified_random(3, (35, 33, 12), mu=0.005, kappa=0.005),
+    "3d_rb": lambda: I.rayleigh_benard(3, (20, 20, 10), amp=1e-3),
+}
+
+
+@pytest.mark.parametrize("case", sorted(CASES))
+def test_fp64_matches_oracle(case):
+    prob, U = CASES[case]()
+    n = 20
+    ref, t_ref, dts = O.run(prob, U, n, return_dt=True)
+    V, d = gpu_run(prob, U, n)
+    errs = field_errors(prob, V, ref)
+    assert max(errs) <= F64_TOL, errs
+    assert d["t"] == pytest.approx(t_ref, rel=1e-13)
+    assert d["dt"] == pytest.approx(dts[-1], rel=1e-13)
+    assert d["status"] == 0
+
+
+def test_compute_dt_matches_oracle():
+    ark = _ark()
+    for prob, U in (I.random_periodic(3, (9, 7, 11), seed=3, mu=0.02, kappa=0.03), I.atmosphere((37, 29)),
+                    I.random_periodic(2, (8, 8), mu=3.0)):
+        with ark.Solver(prob, "f64", stream=_stream()) as s:
+            s.set_state(U)
+            assert s.compute_dt() == pytest.approx(O.dt(prob, U), rel=1e-15)
+
+
+def test_fixed_dt_path():
+    prob, U = I.stratified_random(2, (17, 11), mu=0.01, kappa=0.02)
+    dt = 0.5 * O.dt(prob, U)
+    ref, _ = O.run(prob, U, 10, dt_fixed=dt)
+    V, d = gpu_run(prob, U, 10, dt=dt)
+    assert max_error(prob, V, ref) <= F64_TOL
+    assert d["t"] == pytest.approx(10 * dt, rel=1e-14)
+
+
+@pytest.mark.parametrize("low_mach", [1, 0])
+def test_config_atmosphere_128_1000_steps(low_mach):
+    """2D 128 x 128 isothermal atmosphere, 1000 steps: at rest to round-off,
+    mass and energy conserved, equal to the oracle."""
+    prob, U = I.atmosphere((128, 128), low_mach=low_mach)
+    ref, _ = O.run(prob, U, 1000)
+    V, d = gpu_run(prob, U, 1000)
+    assert max_error(prob, V, ref) <= F64_TOL
+    assert d["max_speed"] < 1e-12
+    d0 = O.diagnostics(prob, U)
+    assert abs(d["mass"] - d0["mass"]) <= 1e-13 * d0["mass"]
+    assert abs(d["energy"] - d0["energy"]) <= 1e-13 * d0["energy"]
+
+
+def test_config_rayleigh_benard_256x128():
+    """2D Rayleigh-Benard 256 x 128 at 1.1 Ra_c: 1000 steps equal to the oracle."""
+    prob, U = I.rayleigh_benard(2, (256, 128))
+    ref, t = O.run(prob, U, 1000)
+    V, d = gpu_run(prob, U, 1000)
+    assert max_error(prob, V, ref) <= F64_TOL
+    assert d["t"] == pytest.approx(t, rel=1e-13)
+
+
+def _sample_points(prob, rng, k):
+    pts = []
+    n = prob.n[: prob.dim]
+    for _ in range(k):
+        pts.append(tuple(int(rng.integers(0, n[d])) for d in range(prob.dim)))
+    # faces, edges and corners of the box, tile seams
+    pts.append(tuple(0 for _ in range(prob.dim)))
+    pts.append(tuple(n[d] - 1 for d in range(prob.dim)))
+    pts.append(tuple((15 if d < 2 else n[d] - 2) % n[d] for d in range(prob.dim)))
+    pts.append(tuple((16 if d < 2 else 1) % n[d] for d in range(prob.dim)))
+    return pts
+
+
+@pytest.mark.parametrize("precision", ["f64", "f32split"])
+def test_full_size_3d_rb_sampled(precision):
+    """3D Rayleigh-Benard 512 x 512 x 256 (the benchmark workload and launch
+    shape): one GPU step, compared with the oracle on sampled 2 x 2 x 2 windows."""
+    prob, U = I.rayleigh_benard(3, (512, 512, 256), m=0.1, chi=1.1, Ra=1e7, amp=1e-3, seed=4)
+    V, d = gpu_run(prob, U, 1, precision=precision)
+    dt = d["dt"]
+    assert dt == pytest.approx(O.dt(prob, U), rel=1e-14 if precision == "f64" else 1e-6)
+    rng = np.random.default_rng(0)
+    tol = F64_TOL if precision == "f64" else F32_STEP_TOL
+    for p in _sample_points(prob, rng, 12):
+        lo = [min(p[d], prob.n[d] - 2) for d in range(3)]
+        hi = [lo[d] + 2 for d in range(3)]
+        W = O.step_window(prob, U, dt, lo, hi)
+        sl = (slice(None),) + tuple(slice(lo[d], hi[d]) for d in reversed(range(3)))
+        errs = field_errors(prob, V[sl], W)
+        assert max(errs) <= tol, (p, errs)
+
+
+@pytest.mark.parametrize("case", ["2d_periodic_visc", "2d_strat_noslip_visc", "3d_strat_noslip_visc_ragged", "3d_rb"])
+@pytest.mark.parametrize("precision", ["f32", "f32split"])
+def test_fp32_forms_match_oracle_within_budget(case, precision):
+    prob, U = CASES[case]()
+    n = 20
+    ref, _, dts = O.run(prob, U, n, return_dt=True)
+    V, d = gpu_run(prob, U, n, precision=precision)
+    errs = field_errors(prob, V, ref)
+    assert max(errs) <= n * F32_STEP_TOL, errs
+    assert d["status"] == 0
+
+
+def test_split_keeps_atmosphere_at_rest_and_beats_plain_fp32():
+    """The FP64 base state makes the FP32 form well balanced: the atmosphere at
+    rest stays at rest to FP32 round-off of the deviations, far below plain FP32."""
+    prob, U = I.atmosphere((128, 128))
+    _, d_split = gpu_run(prob, U, 1000, precision="f32split")
+    _, d_f32 = gpu_run(prob, U, 1000, precision="f32")
+    assert d_split["max_speed"] < 1e-10
+    assert d_f32["max_speed"] > 100 * d_split["max_speed"]
+
+
+def test_split_low_mach_gresho_accuracy():
+    """Gresho vortex at Ma = 1e-3 (Sec. 4.2): the split FP32 velocity stays
+    within 1e-4 of the FP64 oracle's after 100 steps; plain FP32 does not."""
+    prob, U = I.gresho(64, mach=1e-3)
+    ref, _ = O.run(prob, U, 100)
+    out = {}
+    for precision in ("f32split", "f32"):
+        V, _ = gpu_run(prob, U, 100, precision=precision)
+        out[precision] = max(np.max(np.abs(V[k] / V[0] - ref[k] / ref[0])) for k in (1, 2))
+    assert out["f32split"] < 1e-4
+    assert out["f32"] > 10 * out["f32split"]
+
+
+def test_run_twice_bitwise_identical():
+    prob, U = I.stratified_random(3, (35, 33, 12), mu=0.005, kappa=0.005)
+    A, da = gpu_run(prob, U, 30)
+    B, db = gpu_run(prob, U, 30)
+    assert np.array_equal(A, B)
+    assert da["t"] == db["t"]
+
+
+def test_uniform_flow_preserved_bitwise_on_gpu():
+    prob, U = I.random_periodic(3, (33, 17, 9), amp=0.0, mu=0.01, kappa=0.01)
+    for d in range(3):
+        U[1 + d] = (0.3 - 0.2 * d) * U[0]
+    U[4] = 1.0 / 0.4 + 0.5 * sum((0.3 - 0.2 * d) ** 2 for d in range(3))
+    V, _ = gpu_run(prob, U, 10)
+    assert np.array_equal(V, U)
+
+
+def test_conservation_at_scale():
+    prob, U = I.random_periodic(3, (64, 64, 64), seed=9, mu=0.01, kappa=0.01)
+    ark = _ark()
+    with ark.Solver(prob, "f64", stream=_stream()) as s:
+        s.set_state(U)
+        d0 = s.diagnostics()
+        s.step(100)
+        d = s.diagnostics()
+    assert abs(d["mass"] - d0["mass"]) <= 1e-13 * d0["mass"]
+    assert abs(d["energy"] - d0["energy"]) <= 1e-13 * d0["energy"]
+    for k in ("mom_x", "mom_y", "mom_z"):
+        assert abs(d[k] - d0[k]) <= 1e-13
+
+
+def test_transpose_symmetry_on_gpu():
+    prob, U = I.random_periodic(2, (40, 24), seed=3, mu=0.01, kappa=0.01)
+    probT = prob.replace(n=(24, 40, 1))
+    UT = np.ascontiguousarray(np.stack([U[0].T, U[2].T, U[1].T, U[3].T]))
+    dt = O.dt(prob, U)
+    V, _ = gpu_run(prob, U, 5, dt=dt)
+    VT, _ = gpu_run(probT, UT, 5, dt=dt)
+    back = np.stack([VT[0].T, VT[2].T, VT[1].T, VT[3].T])
+    assert np.max(np.abs(back - V)) <= 1e-14 * np.max(np.abs(V))
+
+
+def test_device_pointer_state_roundtrip():
+    import torch
+    prob, U = I.rayleigh_benard(2, (64, 32), amp=1e-3)
+    ark = _ark()
+    Ud = torch.from_numpy(U).cuda()
+    with ark.Solver(prob, "f32split", stream=_stream()) as s:
+        s.set_state(Ud)
+        out = torch.empty_like(Ud)
+        s.get_state(out)
+        torch.cuda.synchronize()
+    assert torch.max(torch.abs(out - Ud)).item() <= 1e-6 * torch.max(torch.abs(Ud)).item()
+
+
+def test_nonphysical_state_is_reported():
+    """A fault injected on the host (negative density in the input) is reported
+    by status, not by a device trap."""
+    ark = _ark()
+    prob, U = I.random_periodic(2, (16, 16), seed=1)
+    U[0, 3, 4] = -1.0
+    with ark.Solver(prob, "f64", stream=_stream()) as s:
+        s.set_state(U)
+        s.step(1, dt=1e-4)
+        with pytest.raises(ark.ArkError) as ei:
+            s.diagnostics()
+        assert ei.value.status == ark.ARK_ERR_NONPHYSICAL
+        with pytest.raises(ark.ArkError):
+            s.sync(10.0)
+
+
+def test_bounded_wait_times_out_then_recovers():
+    ark = _ark()
+    prob, U = I.rayleigh_benard(3, (256, 256, 128), amp=1e-3)
+    with ark.Solver(prob, "f64", stream=_stream()) as s:
+        s.set_state(U)
+        s.step(20)
+        with pytest.raises(ark.ArkError) as ei:
+            s.sync(1e-6)
+        assert ei.value.status == ark.ARK_ERR_TIMEOUT
+        s.sync(120.0)
+        assert s.diagnostics()["step"] == 20
