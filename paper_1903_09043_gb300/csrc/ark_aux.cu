@@ -30,7 +30,7 @@ __device__ __forceinline__ void block_reduce_max(T& v, double* red)
 // (positive doubles order like their bit patterns, so the result does not
 // depend on the order of the blocks).
 template <int D, typename Real, bool SPLIT, bool VISC>
-__global__ void __launch_bounds__(AUX_THREADS) wave_rate_kernel(const StepArgs a, const Real* __restrict__ U,
+__global__ void __launch_bounds__(AUX_THREADS) wave_rate_kernel(const __grid_constant__ StepArgs a, const Real* __restrict__ U,
                                                                   unsigned long long* slot)
 {
     __shared__ double red[AUX_THREADS];

@@ -63,6 +63,7 @@ struct StepCfg {
     static constexpr int N_REAL = O_VFLUX + (VISC ? NV * (NTX + NTY) : 0);
     static constexpr size_t SMEM_BYTES = ((N_REAL * sizeof(Real) + 15) / 16) * 16 + NT * sizeof(double);
 
+    static constexpr int TXV = TX, TYV = TY;
     __device__ static int i2(int lx, int ly) { return (ly + HY) * R2X + (lx + 2); }
     __device__ static int i1(int lx, int ly) { return (ly + H1) * R1X + (lx + 1); }
     __device__ static int ifx(int lx, int ly) { return (ly + H1) * FXX + (lx + 2); }
@@ -75,6 +76,7 @@ template <int D, typename Real>
 struct Cell {
     Real drho, m[D], dW;            // conserved values (deviation form in F32_SPLIT)
     Real rho, u[D], dp, dT, c;      // full rho, velocity, deviation p and T (full in F64/F32), c
+    Real rr;                        // 1 / rho
 };
 
 template <typename Real>
@@ -92,10 +94,13 @@ __device__ __forceinline__ double rsqrt_<double>(double x) { return rsqrt(x); }
 template <>
 __device__ __forceinline__ float rsqrt_<float>(float x) { return rsqrtf(x); }
 
-// Phi at the centre of row r of the gravity axis (Phi = -g x_last).
-__device__ __forceinline__ double phi_row(const StepArgs& a, int r, double dv)
+// Phi at the centre of row r of the gravity axis (Phi = -g x_last), in the
+// state precision (FP32 kernels do no FP64 arithmetic per plane: GB300's FP64
+// rate is 1/64 of its FP32 rate).
+template <typename Real>
+__device__ __forceinline__ Real phi_row(const StepArgs& a, int r, double)
 {
-    return -(a.g * (a.lo_v + (r + 0.5) * dv));
+    return -(Real(a.g) * (Real(a.lo_v) + (Real(r) + Real(0.5)) * Real(a.dx[a.dim - 1])));
 }
 
 template <typename Real, bool SPLIT>
@@ -111,7 +116,7 @@ __device__ __forceinline__ Row<Real> row_info(const StepArgs& a, int r, int nv, 
     } else {
         w.rho0 = Real(0); w.p0 = Real(0); w.T0 = Real(0);
     }
-    w.phi = Real(phi_row(a, r, dv));
+    w.phi = phi_row<Real>(a, r, dv);
     return w;
 }
 
@@ -121,6 +126,7 @@ __device__ __forceinline__ void prim(Cell<D, Real>& c, const Row<Real>& w, Real 
 {
     c.rho = SPLIT ? w.rho0 + c.drho : c.drho;
     const Real rr = rcp(c.rho);
+    c.rr = rr;
     Real ke = Real(0);
 #pragma unroll
     for (int d = 0; d < D; ++d) {
@@ -145,7 +151,8 @@ __device__ __forceinline__ void cons_from_prim(Cell<D, Real>& g, const Row<Real>
     }
     g.dW = g.dp / gm1 + Real(0.5) * ke + g.drho * w.phi;
     const Real p = SPLIT ? w.p0 + g.dp : g.dp;
-    g.c = sqrt(gamma * p / g.rho);
+    g.rr = rcp(g.rho);
+    g.c = sqrt(gamma * p * g.rr);
 }
 
 // Wall ghost (reflective hydrostatic or no-slip fixed-temperature): velocity
@@ -310,12 +317,12 @@ struct Stepper {
         const Row<Real> w0 = row_info<Real, SPLIT>(a, r0, nv, dv);
         const Row<Real> w1g = row_info<Real, SPLIT>(a, g1r, nv, dv);
         const Cell<D, Real> M0 = fetch_h(gx, gy, r0, w0);
-        const Real dphi1 = Real(phi_row(a, g1r, dv) - phi_row(a, r0, dv));
+        const Real dphi1 = phi_row<Real>(a, g1r, dv) - phi_row<Real>(a, r0, dv);
         Cell<D, Real> g1 = wall_ghost<D, Real, SPLIT>(M0, M0, bc, V, Tw, w1g, dphi1, gm1, gamma);
         if (gv == g1r) return g1;
         const Row<Real> w1 = row_info<Real, SPLIT>(a, r1, nv, dv);
         const Cell<D, Real> M1 = fetch_h(gx, gy, r1, w1);
-        const Real dphi2 = Real(phi_row(a, gv, dv) - phi_row(a, g1r, dv));
+        const Real dphi2 = phi_row<Real>(a, gv, dv) - phi_row<Real>(a, g1r, dv);
         return wall_ghost<D, Real, SPLIT>(M1, g1, bc, V, Tw, wg, dphi2, gm1, gamma);
     }
 };
@@ -338,25 +345,65 @@ __device__ __forceinline__ void acoustic_face(Real uL, Real uR, Real dpL, Real d
     dPi = Real(0.5) * (dpL + dpR) - Real(0.5) * a * theta * (uR - uL);
 }
 
+template <int N>
+struct IC {
+    static constexpr int value = N;
+};
+
+// Store one loaded cell (conserved + primitive values) into the plane rings.
+template <class C, int D, typename Real>
+__device__ __forceinline__ void store_cell(const Cell<D, Real>& x, Real* vT, Real* ff, Real* uc, int c, int lx, int ly)
+{
+#pragma unroll
+    for (int d = 0; d < D; ++d) vT[d * C::NR2 + c] = x.u[d];
+    if constexpr (C::NVT > D) vT[D * C::NR2 + c] = x.dT;
+    const Real rc = rcp(x.c);
+    ff[0 * C::NR2 + c] = x.dp;
+    ff[1 * C::NR2 + c] = rc;
+    ff[2 * C::NR2 + c] = x.rho * x.c;
+    ff[3 * C::NR2 + c] = rc * x.rr;
+    if (lx >= -1 && lx <= C::TXV && ly >= -C::H1 && ly < C::R1Y - C::H1) {
+        const int c1 = C::i1(lx, ly);
+        uc[c1] = x.drho;
+#pragma unroll
+        for (int d = 0; d < D; ++d) uc[(1 + d) * C::NR1 + c1] = x.m[d];
+        uc[(D + 1) * C::NR1 + c1] = x.dW;
+    }
+}
+
+// Cells of ghost planes and of tiles that touch the box edge: boundary rules,
+// out of line so that the interior path stays in registers.
+template <int DIM, typename Real, bool SPLIT, bool VISC, int TX, int TY>
+__device__ __noinline__ void slow_cell(const Stepper<DIM, Real, SPLIT, VISC, TX, TY> S, int gx, int gy, int f,
+                                       Real* vT, Real* ff, Real* uc, int c, int lx, int ly)
+{
+    using C = StepCfg<DIM, Real, SPLIT, VISC, TX, TY>;
+    const Cell<DIM, Real> x = S.fetch(gx, gy, f);
+    store_cell<C, DIM, Real>(x, vT, ff, uc, c, lx, ly);
+}
+
 template <int DIM, typename Real, bool SPLIT, bool VISC, int TX, int TY>
 __global__ void __launch_bounds__(TX * TY, sizeof(Real) == 8 ? 1 : 2)
-ark_step_kernel(const StepArgs a)
+ark_step_kernel(const __grid_constant__ StepArgs a)
 {
     using C = StepCfg<DIM, Real, SPLIT, VISC, TX, TY>;
     constexpr int D = DIM, NF = DIM + 2, V = DIM - 1;
-    constexpr int NT = C::NT, NR1 = C::NR1, NR2 = C::NR2;
+    constexpr int NT = C::NT, NR1 = C::NR1, NR2 = C::NR2, NVT = C::NVT;
+    constexpr int NSLOT = (NR2 + NT - 1) / NT;
     extern __shared__ __align__(16) unsigned char smem_raw[];
     Real* sm = reinterpret_cast<Real*>(smem_raw);
     double* red = reinterpret_cast<double*>(smem_raw + ((C::N_REAL * sizeof(Real) + 15) / 16) * 16);
 
-    Stepper<DIM, Real, SPLIT, VISC, TX, TY> S(a);
+    const Stepper<DIM, Real, SPLIT, VISC, TX, TY> S(a);
     const int tid = threadIdx.x;
     const int tile = blockIdx.x;
     const int x0 = (tile % a.tiles_x) * TX;
     const int y0 = D == 3 ? (tile / a.tiles_x) * TY : 0;
     const int z0 = blockIdx.y * a.planes;
     const int z1 = min(z0 + a.planes, S.nv);
-    const int nx = S.nx, ny = S.ny;
+    const int nx = S.nx, ny = S.ny, nv = S.nv;
+    const Real* __restrict__ U = S.U;
+    const long long N = S.N;
 
     // time step of this step (identical in every block)
     double dt_d = a.dt_fixed;
@@ -366,23 +413,49 @@ ark_step_kernel(const StepArgs a)
         *a.time += dt_d;
         *a.dt_last = dt_d;
     }
-    Real lam[3], dtdx[3];
+    Real lam[3];
 #pragma unroll
-    for (int d = 0; d < 3; ++d) {
-        lam[d] = d < D ? Real(dt_d / a.dx[d]) : Real(0);
-        dtdx[d] = lam[d];
-    }
+    for (int d = 0; d < 3; ++d) lam[d] = d < D ? Real(dt_d / a.dx[d]) : Real(0);
     const Real dt = Real(dt_d);
     const Real K = Real(a.K), halfInvK = Real(0.5 / a.K);
     const Real mu = Real(a.mu), kappa = Real(a.kappa), eta = Real(-2.0 / 3.0 * a.mu);
     const Real invdx[3] = {Real(1.0 / a.dx[0]), Real(1.0 / a.dx[1]), Real(1.0 / a.dx[2])};
     const Real* __restrict__ Bt = static_cast<const Real*>(a.base);
-    const int BL = S.nv + 4;
+    const int BL = nv + 4;
+    auto base = [&](int field, int r) -> Real { return SPLIT ? __ldg(Bt + field * BL + r + 2) : Real(0); };
 
     // this thread's output cell
     const int olx = tid % TX, oly = tid / TX;
     const int ogx = x0 + olx, ogy = y0 + oly;
     const bool ocol = ogx < nx && (D == 2 || ogy < ny);
+
+    // this thread's load slots (fixed in-plane positions)
+    int sgx[NSLOT], sgy[NSLOT];
+    bool sin[NSLOT];
+    long long sidx[NSLOT];
+#pragma unroll
+    for (int s = 0; s < NSLOT; ++s) {
+        const int c = tid + s * NT;
+        const int lx = c % C::R2X - 2, ly = c / C::R2X - C::HY;
+        sgx[s] = min(max(x0 + lx, -2), nx + 1);
+        sgy[s] = D == 3 ? min(max(y0 + ly, -2), ny + 1) : 0;
+        sin[s] = c < NR2 && sgx[s] >= 0 && sgx[s] < nx && (D == 2 || (sgy[s] >= 0 && sgy[s] < ny));
+        sidx[s] = D == 3 ? sgx[s] + (long long)nx * sgy[s] : sgx[s];
+    }
+    const long long plane_cells = D == 3 ? (long long)nx * ny : (long long)nx;
+    Real raw[NSLOT][NF];
+    auto prefetch = [&](int p) {
+        if (p < 0 || p >= nv) return;
+#pragma unroll
+        for (int s = 0; s < NSLOT; ++s) {
+            if (sin[s]) {
+                const long long idx = sidx[s] + plane_cells * p;
+#pragma unroll
+                for (int k = 0; k < NF; ++k) raw[s][k] = __ldg(U + k * N + idx);
+            }
+        }
+    };
+    prefetch(z0 - 2);
 
     // register carries along the column
     Real zt_lo[NF];            // transport flux through the lower z face of the output plane
@@ -395,250 +468,229 @@ ark_step_kernel(const StepArgs a)
     Real smax_t = Real(0);
     unsigned status = 0u;
 
-    auto velT = [&](int plane, int comp, int idx) -> Real& {
-        const int s = ((plane % 3) + 3) % 3;
-        return sm[C::O_VELT + (s * C::NVT + comp) * NR2 + idx];
-    };
-    auto facef = [&](int plane, int comp, int idx) -> Real& {
-        return sm[C::O_FACEF + ((plane & 1) * 4 + comp) * NR2 + idx];
-    };
-    auto ucons = [&](int plane, int comp, int idx) -> Real& {
-        return sm[C::O_UCONS + ((plane & 1) * NF + comp) * NR1 + idx];
-    };
-    // z face between planes q and q+1 is stored in slot (q + 1) & 1
-    auto zf = [&](int upper, int comp, int idx) -> Real& {
-        return sm[C::O_ZF + ((upper & 1) * 3 + comp) * NR1 + idx];
-    };
-    auto xyf = [&](int plane, int dir, int comp, int idx) -> Real& {
-        const int base = C::O_XYF + (plane & 1) * 2 * (C::NFX + C::NFY);
-        return sm[base + comp * (C::NFX + C::NFY) + (dir ? C::NFX : 0) + idx];
-    };
-    auto tl = [&](int plane, int comp, int idx) -> Real& {
-        return sm[C::O_TL + ((plane & 1) * (NF + 1) + comp) * NR1 + idx];
-    };
-    auto tflux = [&](int dir, int comp, int idx) -> Real& {
-        return sm[C::O_TFLUX + comp * (C::NTX + C::NTY) + (dir ? C::NTX : 0) + idx];
-    };
-    auto vflux = [&](int dir, int comp, int idx) -> Real& {
-        return sm[C::O_VFLUX + comp * (C::NTX + C::NTY) + (dir ? C::NTX : 0) + idx];
-    };
-    auto base = [&](int field, int r) -> Real { return SPLIT ? __ldg(Bt + field * BL + r + 2) : Real(0); };
-
     for (int f = z0 - 2; f <= z1 + 1; ++f) {
-        // ---------------- A: load plane f, primitives ----------------
-        const bool fin = f >= 0 && f < S.nv;
-        const Row<Real> wf = row_info<Real, SPLIT>(a, fin ? f : 0, S.nv, S.dv);
-        for (int c = tid; c < NR2; c += NT) {
-            const int lx = c % C::R2X - 2, ly = c / C::R2X - C::HY;
-            int gx = x0 + lx, gy = y0 + ly;
-            gx = min(max(gx, -2), nx + 1);
-            if (D == 3) gy = min(max(gy, -2), ny + 1);
-            Cell<D, Real> cell;
-            if (fin && gx >= 0 && gx < nx && (D == 2 || (gy >= 0 && gy < ny))) cell = S.load_in(gx, gy, f, wf);
-            else cell = S.fetch(gx, gy, f);
+        // ring slots of this iteration
+        const int s3 = ((f % 3) + 3) % 3;
+        Real* const vT_f = sm + C::O_VELT + s3 * NVT * NR2;
+        Real* const vT_f1 = sm + C::O_VELT + ((s3 + 2) % 3) * NVT * NR2;
+        Real* const vT_f2 = sm + C::O_VELT + ((s3 + 1) % 3) * NVT * NR2;
+        Real* const ff_f = sm + C::O_FACEF + (f & 1) * 4 * NR2;
+        Real* const ff_f1 = sm + C::O_FACEF + ((f - 1) & 1) * 4 * NR2;
+        Real* const uc_f = sm + C::O_UCONS + (f & 1) * NF * NR1;
+        Real* const uc_f1 = sm + C::O_UCONS + ((f - 1) & 1) * NF * NR1;
+        Real* const zf_up = sm + C::O_ZF + (f & 1) * 3 * NR1;          // face (f-1, f)
+        Real* const zf_lo = sm + C::O_ZF + ((f - 1) & 1) * 3 * NR1;    // face (f-2, f-1)
+        Real* const xy_f1 = sm + C::O_XYF + ((f - 1) & 1) * 2 * (C::NFX + C::NFY);
+        Real* const xy_f2 = sm + C::O_XYF + ((f - 2) & 1) * 2 * (C::NFX + C::NFY);
+        Real* const tl_f1 = sm + C::O_TL + ((f - 1) & 1) * (NF + 1) * NR1;
+        Real* const tl_f2 = sm + C::O_TL + ((f - 2) & 1) * (NF + 1) * NR1;
+        Real* const tfx = sm + C::O_TFLUX;
+        Real* const vfx = sm + C::O_VFLUX;
+        constexpr int XYS = C::NFX + C::NFY;     // component stride of the in-plane face arrays
+        constexpr int TFS = C::NTX + C::NTY;     // component stride of the output-face arrays
+
+        // ---------------- A: plane f (primitives), prefetch of plane f + 1 ----------------
+        const bool fin = f >= 0 && f < nv;
+        const Row<Real> wf = row_info<Real, SPLIT>(a, fin ? f : 0, nv, S.dv);
 #pragma unroll
-            for (int d = 0; d < D; ++d) velT(f, d, c) = cell.u[d];
-            if constexpr (VISC) velT(f, D, c) = cell.dT;
-            const Real rc = rcp(cell.c);
-            facef(f, 0, c) = cell.dp;
-            facef(f, 1, c) = rc;
-            facef(f, 2, c) = cell.rho * cell.c;
-            facef(f, 3, c) = rc * rcp(cell.rho);
-            if (lx >= -1 && lx <= TX && ly >= -C::H1 && ly < TY + C::H1) {
-                const int c1 = C::i1(lx, ly);
-                ucons(f, 0, c1) = cell.drho;
+        for (int s = 0; s < NSLOT; ++s) {
+            const int c = tid + s * NT;
+            if (c < NR2) {
+                const int lx = c % C::R2X - 2, ly = c / C::R2X - C::HY;
+                if (fin && sin[s]) {
+                    Cell<D, Real> x;
+                    x.drho = raw[s][0];
 #pragma unroll
-                for (int d = 0; d < D; ++d) ucons(f, 1 + d, c1) = cell.m[d];
-                ucons(f, D + 1, c1) = cell.dW;
+                    for (int d = 0; d < D; ++d) x.m[d] = raw[s][1 + d];
+                    x.dW = raw[s][D + 1];
+                    prim<D, Real, SPLIT>(x, wf, S.gm1, S.gamma);
+                    store_cell<C, D, Real>(x, vT_f, ff_f, uc_f, c, lx, ly);
+                } else {
+                    slow_cell<DIM, Real, SPLIT, VISC, TX, TY>(S, sgx[s], sgy[s], f, vT_f, ff_f, uc_f, c, lx, ly);
+                }
             }
         }
+        prefetch(f + 1);
         __syncthreads();
 
         // ---------------- B: acoustic faces ----------------
-        const int q1 = f - 1;   // plane of the in-plane faces and of the tilde states
         if (f >= z0) {
             // in-plane x faces of plane f-1 bounding R1 cells
             for (int e = tid; e < C::NFX; e += NT) {
                 const int lx = e % C::FXX - 2, ly = e / C::FXX - C::H1;
-                const int iL = C::i2(lx, ly), iR = C::i2(lx + 1, ly);
+                const int iL = C::i2(lx, ly), iR = iL + 1;
                 Real us, dPi;
-                acoustic_face<Real>(velT(q1, 0, iL), velT(q1, 0, iR), facef(q1, 0, iL), facef(q1, 0, iR),
-                                    facef(q1, 2, iL), facef(q1, 2, iR), facef(q1, 3, iL), facef(q1, 3, iR),
-                                    facef(q1, 1, iL), facef(q1, 1, iR), Real(0), Real(0), K, halfInvK,
-                                    a.low_mach, us, dPi);
-                xyf(q1, 0, 0, e) = us;
-                xyf(q1, 0, 1, e) = dPi;
+                acoustic_face<Real>(vT_f1[iL], vT_f1[iR], ff_f1[iL], ff_f1[iR], ff_f1[2 * NR2 + iL],
+                                    ff_f1[2 * NR2 + iR], ff_f1[3 * NR2 + iL], ff_f1[3 * NR2 + iR], ff_f1[NR2 + iL],
+                                    ff_f1[NR2 + iR], Real(0), Real(0), K, halfInvK, a.low_mach, us, dPi);
+                xy_f1[e] = us;
+                xy_f1[XYS + e] = dPi;
             }
             if constexpr (D == 3) {
                 for (int e = tid; e < C::NFY; e += NT) {
                     const int lx = e % C::R1X - 1, ly = e / C::R1X - 2;
-                    const int iL = C::i2(lx, ly), iR = C::i2(lx, ly + 1);
+                    const int iL = C::i2(lx, ly), iR = iL + C::R2X;
                     Real us, dPi;
-                    acoustic_face<Real>(velT(q1, 1, iL), velT(q1, 1, iR), facef(q1, 0, iL), facef(q1, 0, iR),
-                                        facef(q1, 2, iL), facef(q1, 2, iR), facef(q1, 3, iL), facef(q1, 3, iR),
-                                        facef(q1, 1, iL), facef(q1, 1, iR), Real(0), Real(0), K, halfInvK,
+                    acoustic_face<Real>(vT_f1[NR2 + iL], vT_f1[NR2 + iR], ff_f1[iL], ff_f1[iR], ff_f1[2 * NR2 + iL],
+                                        ff_f1[2 * NR2 + iR], ff_f1[3 * NR2 + iL], ff_f1[3 * NR2 + iR],
+                                        ff_f1[NR2 + iL], ff_f1[NR2 + iR], Real(0), Real(0), K, halfInvK,
                                         a.low_mach, us, dPi);
-                    xyf(q1, 1, 0, e) = us;
-                    xyf(q1, 1, 1, e) = dPi;
+                    xy_f1[C::NFX + e] = us;
+                    xy_f1[XYS + C::NFX + e] = dPi;
                 }
             }
         }
         if (f >= z0 - 1) {
             // faces between planes f-1 (low side) and f (high side), over R1 cells
-            const Real dphi = Real(phi_row(a, f, S.dv) - phi_row(a, f - 1, S.dv));
+            const Real dphi = phi_row<Real>(a, f, S.dv) - phi_row<Real>(a, f - 1, S.dv);
             const Real r0f = base(B_R0F, f - 1);
             for (int c = tid; c < NR1; c += NT) {
                 const int lx = c % C::R1X - 1, ly = c / C::R1X - C::H1;
                 const int i = C::i2(lx, ly);
-                const Real dS = Real(-0.5) * (ucons(q1, 0, c) + ucons(f, 0, c)) * dphi;
+                const Real dS = Real(-0.5) * (uc_f1[c] + uc_f[c]) * dphi;
                 Real us, dPi;
-                acoustic_face<Real>(velT(q1, V, i), velT(f, V, i), facef(q1, 0, i), facef(f, 0, i),
-                                    facef(q1, 2, i), facef(f, 2, i), facef(q1, 3, i), facef(f, 3, i),
-                                    facef(q1, 1, i), facef(f, 1, i), r0f, dS, K, halfInvK, a.low_mach, us, dPi);
-                zf(f, 0, c) = us;
-                zf(f, 1, c) = dPi;
-                zf(f, 2, c) = dS;
+                acoustic_face<Real>(vT_f1[V * NR2 + i], vT_f[V * NR2 + i], ff_f1[i], ff_f[i], ff_f1[2 * NR2 + i],
+                                    ff_f[2 * NR2 + i], ff_f1[3 * NR2 + i], ff_f[3 * NR2 + i], ff_f1[NR2 + i],
+                                    ff_f[NR2 + i], r0f, dS, K, halfInvK, a.low_mach, us, dPi);
+                zf_up[c] = us;
+                zf_up[NR1 + c] = dPi;
+                zf_up[2 * NR1 + c] = dS;
             }
         }
         __syncthreads();
 
         // ---------------- C: tilde states of plane f-1; dissipative fluxes ----------------
+        const int q1 = f - 1;
         if (f >= z0) {
             const Real rho0 = base(B_RHO0, q1), H0 = base(B_H0, q1), Q0 = base(B_Q0, q1);
             const Real dPp = base(B_DPP, q1), dPm = base(B_DPM, q1);
             for (int c = tid; c < NR1; c += NT) {
                 const int lx = c % C::R1X - 1, ly = c / C::R1X - C::H1;
-                // in-plane face indices
-                const int exp_ = C::ifx(lx, ly), exm = C::ifx(lx - 1, ly);
-                Real usx_p = xyf(q1, 0, 0, exp_), usx_m = xyf(q1, 0, 0, exm);
-                Real pix_p = xyf(q1, 0, 1, exp_), pix_m = xyf(q1, 0, 1, exm);
-                const Real usz_p = zf(f, 0, c), usz_m = zf(q1, 0, c);
-                const Real piz_p = zf(f, 1, c), piz_m = zf(q1, 1, c);
-                const Real dSz_p = zf(f, 2, c), dSz_m = zf(q1, 2, c);
+                const int exp_ = C::ifx(lx, ly), exm = exp_ - 1;
+                const Real usx_p = xy_f1[exp_], usx_m = xy_f1[exm];
+                const Real pix_p = xy_f1[XYS + exp_], pix_m = xy_f1[XYS + exm];
+                const Real usz_p = zf_up[c], usz_m = zf_lo[c];
+                const Real piz_p = zf_up[NR1 + c], piz_m = zf_lo[NR1 + c];
+                const Real dSz_p = zf_up[2 * NR1 + c], dSz_m = zf_lo[2 * NR1 + c];
                 Real ell = lam[0] * (usx_p - usx_m);
                 Real m_t[D];
-                m_t[0] = ucons(q1, 1, c) - lam[0] * (pix_p - pix_m);
-                Real W_t = ucons(q1, D + 1, c) - lam[0] * (pix_p * usx_p - pix_m * usx_m);
+                m_t[0] = uc_f1[NR1 + c] - lam[0] * (pix_p - pix_m);
+                Real W_t = uc_f1[(D + 1) * NR1 + c] - lam[0] * (pix_p * usx_p - pix_m * usx_m);
                 if constexpr (D == 3) {
-                    const int eyp = C::ify(lx, ly), eym = C::ify(lx, ly - 1);
-                    const Real usy_p = xyf(q1, 1, 0, eyp), usy_m = xyf(q1, 1, 0, eym);
-                    const Real piy_p = xyf(q1, 1, 1, eyp), piy_m = xyf(q1, 1, 1, eym);
+                    const int eyp = C::NFX + C::ify(lx, ly), eym = eyp - C::R1X;
+                    const Real usy_p = xy_f1[eyp], usy_m = xy_f1[eym];
+                    const Real piy_p = xy_f1[XYS + eyp], piy_m = xy_f1[XYS + eym];
                     ell += lam[1] * (usy_p - usy_m);
-                    m_t[1] = ucons(q1, 2, c) - lam[1] * (piy_p - piy_m);
+                    m_t[1] = uc_f1[2 * NR1 + c] - lam[1] * (piy_p - piy_m);
                     W_t -= lam[1] * (piy_p * usy_p - piy_m * usy_m);
                 }
                 ell += lam[V] * (usz_p - usz_m);
-                m_t[V] = ucons(q1, 1 + V, c) - lam[V] * (piz_p - piz_m) + lam[V] * Real(0.5) * (dSz_p + dSz_m);
+                m_t[V] = uc_f1[(1 + V) * NR1 + c] - lam[V] * (piz_p - piz_m) + lam[V] * Real(0.5) * (dSz_p + dSz_m);
                 if constexpr (SPLIT) m_t[V] -= lam[V] * Q0;
                 W_t -= lam[V] * (piz_p * usz_p - piz_m * usz_m);
                 if constexpr (SPLIT) W_t -= lam[V] * (dPp * usz_p - dPm * usz_m) + H0 * ell;
                 const Real L = Real(1) + ell;
                 const Real rL = rcp(L);
-                Real rho_t = SPLIT ? (ucons(q1, 0, c) - rho0 * ell) * rL : ucons(q1, 0, c) * rL;
-                tl(q1, 0, c) = rho_t;
+                tl_f1[c] = SPLIT ? (uc_f1[c] - rho0 * ell) * rL : uc_f1[c] * rL;
 #pragma unroll
-                for (int d = 0; d < D; ++d) tl(q1, 1 + d, c) = m_t[d] * rL;
-                tl(q1, D + 1, c) = W_t * rL;
-                tl(q1, NF, c) = L;
-                const bool valid = (x0 + lx) >= 0 && (x0 + lx) < nx && (D == 2 || ((y0 + ly) >= 0 && (y0 + ly) < ny)) &&
-                                   q1 >= 0 && q1 < S.nv;
+                for (int d = 0; d < D; ++d) tl_f1[(1 + d) * NR1 + c] = m_t[d] * rL;
+                tl_f1[(D + 1) * NR1 + c] = W_t * rL;
+                tl_f1[NF * NR1 + c] = L;
+                const bool valid = (x0 + lx) >= 0 && (x0 + lx) < nx &&
+                                   (D == 2 || ((y0 + ly) >= 0 && (y0 + ly) < ny)) && q1 >= 0 && q1 < nv;
                 if (valid && !(L > Real(0))) status |= ST_LTILDE;
             }
         }
         if constexpr (VISC) {
-            // dissipative fluxes (Sec. 2.2) from U^n: in-plane faces of plane f-1's output cells,
-            // with tangential derivatives averaged over the two cells of the face
+            // dissipative fluxes (Sec. 2.2) from U^n through the in-plane faces of plane
+            // f-1's output cells; tangential derivatives averaged over the face's two cells
             if (f >= z0 + 1 && f <= z1) {
-                const int qm = f - 2, q0 = f - 1, qp = f;
-                for (int e = tid; e < C::NTX + C::NTY; e += NT) {
-                    const int dir = e < C::NTX ? 0 : 1;
-                    int lxL, lyL, lxR, lyR;
-                    if (dir == 0) {
-                        lxL = e % (TX + 1) - 1; lyL = e / (TX + 1); lxR = lxL + 1; lyR = lyL;
-                    } else {
-                        const int e2 = e - C::NTX;
-                        lxL = e2 % TX; lyL = e2 / TX - 1; lxR = lxL; lyR = lyL + 1;
-                    }
-                    const int iL = C::i2(lxL, lyL), iR = C::i2(lxR, lyR);
-                    Real grad[3][3];   // grad[a][q] = d u_q / d x_a at the face
+                auto face = [&](auto dirc, int lxL, int lyL, int te) {
+                    constexpr int dir = decltype(dirc)::value;
+                    constexpr int sh = dir == 0 ? 1 : C::R2X;
+                    const int iL = C::i2(lxL, lyL), iR = iL + sh;
+                    Real grad[3][3];
 #pragma unroll
                     for (int aa = 0; aa < 3; ++aa)
 #pragma unroll
-                        for (int q = 0; q < 3; ++q) grad[aa][q] = Real(0);
-                    const Real ind = invdx[dir];
+                        for (int qq = 0; qq < 3; ++qq) grad[aa][qq] = Real(0);
 #pragma unroll
-                    for (int q = 0; q < D; ++q) grad[dir][q] = (velT(q0, q, iR) - velT(q0, q, iL)) * ind;
-                    // tangential in-plane direction (3D only)
+                    for (int qq = 0; qq < D; ++qq) grad[dir][qq] = (vT_f1[qq * NR2 + iR] - vT_f1[qq * NR2 + iL]) * invdx[dir];
                     if constexpr (D == 3) {
-                        const int t = 1 - dir;
-                        const int sx = t == 0 ? 1 : 0, sy = t == 1 ? 1 : 0;
-                        const int Lp = C::i2(lxL + sx, lyL + sy), Lm = C::i2(lxL - sx, lyL - sy);
-                        const int Rp = C::i2(lxR + sx, lyR + sy), Rm = C::i2(lxR - sx, lyR - sy);
+                        constexpr int t = 1 - dir;
+                        constexpr int st = t == 0 ? 1 : C::R2X;
 #pragma unroll
-                        for (int q = 0; q < D; ++q)
-                            grad[t][q] = Real(0.25) *
-                                         ((velT(q0, q, Lp) - velT(q0, q, Lm)) + (velT(q0, q, Rp) - velT(q0, q, Rm))) *
-                                         invdx[t];
+                        for (int qq = 0; qq < D; ++qq)
+                            grad[t][qq] = Real(0.25) *
+                                          ((vT_f1[qq * NR2 + iL + st] - vT_f1[qq * NR2 + iL - st]) +
+                                           (vT_f1[qq * NR2 + iR + st] - vT_f1[qq * NR2 + iR - st])) *
+                                          invdx[t];
                     }
-                    // tangential along the gravity axis: planes f and f-2
 #pragma unroll
-                    for (int q = 0; q < D; ++q)
-                        grad[V][q] = Real(0.25) *
-                                     ((velT(qp, q, iL) - velT(qm, q, iL)) + (velT(qp, q, iR) - velT(qm, q, iR))) *
-                                     invdx[V];
+                    for (int qq = 0; qq < D; ++qq)
+                        grad[V][qq] = Real(0.25) *
+                                      ((vT_f[qq * NR2 + iL] - vT_f2[qq * NR2 + iL]) +
+                                       (vT_f[qq * NR2 + iR] - vT_f2[qq * NR2 + iR])) *
+                                      invdx[V];
                     Real divu = Real(0);
 #pragma unroll
                     for (int aa = 0; aa < D; ++aa) divu += grad[aa][aa];
                     Real work = Real(0);
 #pragma unroll
-                    for (int q = 0; q < D; ++q) {
-                        Real tau = mu * (grad[dir][q] + grad[q][dir]);
-                        if (q == dir) tau += eta * divu;
-                        work += tau * Real(0.5) * (velT(q0, q, iL) + velT(q0, q, iR));
-                        vflux(dir, q, dir ? e - C::NTX : e) = tau;
+                    for (int qq = 0; qq < D; ++qq) {
+                        Real tau = mu * (grad[dir][qq] + grad[qq][dir]);
+                        if (qq == dir) tau += eta * divu;
+                        work += tau * Real(0.5) * (vT_f1[qq * NR2 + iL] + vT_f1[qq * NR2 + iR]);
+                        vfx[qq * TFS + (dir ? C::NTX : 0) + te] = tau;
                     }
-                    const Real heat = kappa * (velT(q0, D, iR) - velT(q0, D, iL)) * ind;
-                    vflux(dir, D, dir ? e - C::NTX : e) = work + heat;
+                    const Real heat = kappa * (vT_f1[D * NR2 + iR] - vT_f1[D * NR2 + iL]) * invdx[dir];
+                    vfx[D * TFS + (dir ? C::NTX : 0) + te] = work + heat;
+                };
+                for (int e = tid; e < C::NTX + C::NTY; e += NT) {
+                    if (e < C::NTX) face(IC<0>{}, e % (TX + 1) - 1, e / (TX + 1), e);
+                    else if constexpr (D == 3) {
+                        const int e2 = e - C::NTX;
+                        face(IC<1>{}, e2 % TX, e2 / TX - 1, e2);
+                    }
                 }
             }
         }
         // z-face (f-1, f) dissipative flux of this thread's column
         Real zv_new[C::NV];
 #pragma unroll
-        for (int q = 0; q < C::NV; ++q) zv_new[q] = Real(0);
+        for (int k = 0; k < C::NV; ++k) zv_new[k] = Real(0);
         if constexpr (VISC) {
             if (f >= z0 && f <= z1) {
                 const int iL = C::i2(olx, oly);
-                const int q0 = f - 1, qp = f;
                 Real grad[3][3];
 #pragma unroll
                 for (int aa = 0; aa < 3; ++aa)
 #pragma unroll
-                    for (int q = 0; q < 3; ++q) grad[aa][q] = Real(0);
+                    for (int qq = 0; qq < 3; ++qq) grad[aa][qq] = Real(0);
 #pragma unroll
-                for (int q = 0; q < D; ++q) grad[V][q] = (velT(qp, q, iL) - velT(q0, q, iL)) * invdx[V];
+                for (int qq = 0; qq < D; ++qq) grad[V][qq] = (vT_f[qq * NR2 + iL] - vT_f1[qq * NR2 + iL]) * invdx[V];
 #pragma unroll
                 for (int t = 0; t < D - 1; ++t) {
-                    const int sx = t == 0 ? 1 : 0, sy = t == 1 ? 1 : 0;
-                    const int Pp = C::i2(olx + sx, oly + sy), Pm = C::i2(olx - sx, oly - sy);
+                    const int st = t == 0 ? 1 : C::R2X;
 #pragma unroll
-                    for (int q = 0; q < D; ++q)
-                        grad[t][q] = Real(0.25) *
-                                     ((velT(q0, q, Pp) - velT(q0, q, Pm)) + (velT(qp, q, Pp) - velT(qp, q, Pm))) *
-                                     invdx[t];
+                    for (int qq = 0; qq < D; ++qq)
+                        grad[t][qq] = Real(0.25) *
+                                      ((vT_f1[qq * NR2 + iL + st] - vT_f1[qq * NR2 + iL - st]) +
+                                       (vT_f[qq * NR2 + iL + st] - vT_f[qq * NR2 + iL - st])) *
+                                      invdx[t];
                 }
                 Real divu = Real(0);
 #pragma unroll
                 for (int aa = 0; aa < D; ++aa) divu += grad[aa][aa];
                 Real work = Real(0);
 #pragma unroll
-                for (int q = 0; q < D; ++q) {
-                    Real tau = mu * (grad[V][q] + grad[q][V]);
-                    if (q == V) tau += eta * divu;
-                    work += tau * Real(0.5) * (velT(q0, q, iL) + velT(qp, q, iL));
-                    zv_new[q] = tau;
+                for (int qq = 0; qq < D; ++qq) {
+                    Real tau = mu * (grad[V][qq] + grad[qq][V]);
+                    if (qq == V) tau += eta * divu;
+                    work += tau * Real(0.5) * (vT_f1[qq * NR2 + iL] + vT_f[qq * NR2 + iL]);
+                    zv_new[qq] = tau;
                 }
-                zv_new[D] = work + kappa * (velT(qp, D, iL) - velT(q0, D, iL)) * invdx[V];
+                zv_new[D] = work + kappa * (vT_f[D * NR2 + iL] - vT_f1[D * NR2 + iL]) * invdx[V];
             }
         }
         __syncthreads();
@@ -651,34 +703,34 @@ ark_step_kernel(const StepArgs a)
         if constexpr (VISC) {
             if (f >= z0 + 1 && f <= z1) {
                 // in-plane viscous divergence of plane f-1 for this column
+                const int ex = C::itx(olx, oly);
 #pragma unroll
-                for (int k = 0; k < C::NV; ++k)
-                    dxy_new[k] = (vflux(0, k, C::itx(olx, oly)) - vflux(0, k, C::itx(olx - 1, oly))) * dtdx[0];
+                for (int k = 0; k < C::NV; ++k) dxy_new[k] = (vfx[k * TFS + ex] - vfx[k * TFS + ex - 1]) * lam[0];
                 if constexpr (D == 3) {
+                    const int ey = C::NTX + C::ity(olx, oly);
 #pragma unroll
-                    for (int k = 0; k < C::NV; ++k)
-                        dxy_new[k] += (vflux(1, k, C::ity(olx, oly)) - vflux(1, k, C::ity(olx, oly - 1))) * dtdx[1];
+                    for (int k = 0; k < C::NV; ++k) dxy_new[k] += (vfx[k * TFS + ey] - vfx[k * TFS + ey - TX]) * lam[1];
                 }
             }
         }
         if (f >= z0 + 2) {
             // upwind transport fluxes through the in-plane faces of the output cells
             for (int e = tid; e < C::NTX + C::NTY; e += NT) {
-                const int dir = e < C::NTX ? 0 : 1;
-                int lxL, lyL, lxR, lyR, fe;
-                if (dir == 0) {
-                    lxL = e % (TX + 1) - 1; lyL = e / (TX + 1); lxR = lxL + 1; lyR = lyL;
+                int lxL, lyL, fe, upR;
+                if (e < C::NTX) {
+                    lxL = e % (TX + 1) - 1; lyL = e / (TX + 1);
                     fe = C::ifx(lxL, lyL);
+                    upR = 1;
                 } else {
                     const int e2 = e - C::NTX;
-                    lxL = e2 % TX; lyL = e2 / TX - 1; lxR = lxL; lyR = lyL + 1;
-                    fe = C::ify(lxL, lyL);
+                    lxL = e2 % TX; lyL = e2 / TX - 1;
+                    fe = C::NFX + C::ify(lxL, lyL);
+                    upR = C::R1X;
                 }
-                const Real us = xyf(q, dir, 0, fe);
-                const int up = us >= Real(0) ? C::i1(lxL, lyL) : C::i1(lxR, lyR);
-                const int te = dir ? e - C::NTX : e;
+                const Real us = xy_f2[fe];
+                const int up = C::i1(lxL, lyL) + (us >= Real(0) ? 0 : upR);
 #pragma unroll
-                for (int k = 0; k < NF; ++k) tflux(dir, k, te) = tl(q, k, up) * us;
+                for (int k = 0; k < NF; ++k) tfx[k * TFS + e] = tl_f2[k * NR1 + up] * us;
             }
         }
         Real zt_hi[NF];
@@ -688,10 +740,10 @@ ark_step_kernel(const StepArgs a)
         if (f >= z0 + 1) {
             // transport flux through the face between planes f-2 and f-1 of this column
             const int c1 = C::i1(olx, oly);
-            us_hi = zf(f - 1, 0, c1);
-            const int src = us_hi >= Real(0) ? (f - 2) : (f - 1);
+            us_hi = zf_lo[c1];
+            const Real* src = us_hi >= Real(0) ? tl_f2 : tl_f1;
 #pragma unroll
-            for (int k = 0; k < NF; ++k) zt_hi[k] = tl(src, k, c1) * us_hi;
+            for (int k = 0; k < NF; ++k) zt_hi[k] = src[k * NR1 + c1] * us_hi;
             if constexpr (SPLIT) {
                 // base-state part of the upwind value relative to the row below (plane f-2)
                 if (!(us_hi >= Real(0))) {
@@ -703,29 +755,27 @@ ark_step_kernel(const StepArgs a)
         __syncthreads();
         if (f >= z0 + 2) {
             const int c1 = C::i1(olx, oly);
-            const Real L = tl(q, NF, c1);
+            const Real L = tl_f2[NF * NR1 + c1];
+            const int ex = C::itx(olx, oly);
+            const int ey = C::NTX + C::ity(olx, oly);
             Real nb[NF];
 #pragma unroll
             for (int k = 0; k < NF; ++k) {
-                Real acc = tl(q, k, c1) * L;
-                acc -= lam[0] * (tflux(0, k, C::itx(olx, oly)) - tflux(0, k, C::itx(olx - 1, oly)));
-                if constexpr (D == 3)
-                    acc -= lam[1] * (tflux(1, k, C::ity(olx, oly)) - tflux(1, k, C::ity(olx, oly - 1)));
+                Real acc = tl_f2[k * NR1 + c1] * L;
+                acc -= lam[0] * (tfx[k * TFS + ex] - tfx[k * TFS + ex - 1]);
+                if constexpr (D == 3) acc -= lam[1] * (tfx[k * TFS + ey] - tfx[k * TFS + ey - TX]);
                 nb[k] = acc;
             }
-            // flux through the upper z face uses the base of row q; the lower face
-            // flux (computed relative to row q-1) is shifted to row q's base
+            // the flux through the upper z face is relative to row q's base; the lower
+            // face's flux (computed relative to row q-1) is shifted to row q's base
             Real lowfix[NF];
 #pragma unroll
             for (int k = 0; k < NF; ++k) lowfix[k] = zt_lo[k];
             if constexpr (SPLIT) {
-                // lower face, upwind from below (row q-1): value relative to row q
-                // is b~ + (b0_{q-1} - b0_q); from above it is already relative to row q
                 if (us_lo >= Real(0)) {
                     lowfix[0] += base(B_DRM, q) * us_lo;
                     lowfix[D + 1] += base(B_DWM, q) * us_lo;
                 } else {
-                    // the carried flux was shifted to row q-1 by B_DRP of row q-1; undo it
                     lowfix[0] -= base(B_DRP, q - 1) * us_lo;
                     lowfix[D + 1] -= base(B_DWP, q - 1) * us_lo;
                 }
@@ -734,21 +784,16 @@ ark_step_kernel(const StepArgs a)
             for (int k = 0; k < NF; ++k) nb[k] -= lam[V] * (zt_hi[k] - lowfix[k]);
             if constexpr (VISC) {
 #pragma unroll
-                for (int k = 0; k < C::NV; ++k) {
-                    const Real dv_ = dxy_prev[k] + (zvB[k] - zvA[k]) * dtdx[V];
-                    nb[1 + k] += dv_;   // k < D: momentum m_k, k == D: energy (index D + 1)
-                }
+                for (int k = 0; k < C::NV; ++k) nb[1 + k] += dxy_prev[k] + (zvB[k] - zvA[k]) * lam[V];
                 if constexpr (SPLIT) nb[D + 1] += dt * base(B_DQ0, q);
             }
-            // store U^{n+1}
             if (ocol) {
                 Real* Uo = static_cast<Real*>(a.Uout);
-                const long long idx = D == 3 ? ogx + (long long)nx * (ogy + (long long)ny * q)
-                                             : ogx + (long long)nx * q;
+                const long long idx = D == 3 ? ogx + (long long)nx * (ogy + (long long)ny * q) : ogx + (long long)nx * q;
 #pragma unroll
-                for (int k = 0; k < NF; ++k) Uo[k * S.N + idx] = nb[k];
+                for (int k = 0; k < NF; ++k) Uo[k * N + idx] = nb[k];
                 // CFL wave rate of U^{n+1} (next step's dt) and physical checks
-                const Row<Real> w = row_info<Real, SPLIT>(a, q, S.nv, S.dv);
+                const Row<Real> w = row_info<Real, SPLIT>(a, q, nv, S.dv);
                 Real p, rho;
                 const Real sh = wave_rate<D, Real, SPLIT, VISC>(nb, w, S.gm1, S.gamma, invdx, mu, kappa, p, rho);
                 if (!(sh <= smax_t)) smax_t = (sh == sh) ? sh : smax_t;

@@ -27,18 +27,20 @@ def sound_speed(prob, U):
     return np.sqrt(prob.gamma * np.abs(p) / rho)
 
 
-def field_errors(prob, A, ref):
+def floors(prob, U):
+    """(s_rho, s_m, s_W) of a whole state."""
+    rho_max = float(np.max(np.abs(U[0])))
+    return rho_max, rho_max * float(np.max(sound_speed(prob, U))), float(np.max(np.abs(U[prob.dim + 1])))
+
+
+def field_errors(prob, A, ref, fl=None):
+    """Per-field relative L-infinity; ``fl`` overrides the floors (for windows of a state)."""
     dim = prob.dim
-    rho_max = np.max(np.abs(ref[0]))
-    c_max = np.max(sound_speed(prob, ref))
+    if fl is None:
+        fl = floors(prob, ref)
     errs = []
     for f in range(ref.shape[0]):
-        if f == 0:
-            floor = rho_max
-        elif f <= dim:
-            floor = rho_max * c_max
-        else:
-            floor = np.max(np.abs(ref[f]))
+        floor = fl[0] if f == 0 else (fl[1] if f <= dim else fl[2])
         scale = max(np.max(np.abs(ref[f])), floor)
         errs.append(float(np.max(np.abs(A[f] - ref[f])) / scale))
     return errs

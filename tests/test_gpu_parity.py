@@ -10,7 +10,7 @@ import pytest
 
 import oracle as O
 from paper_1903_09043_gb300 import inputs as I
-from parity import F32_STEP_TOL, F64_TOL, field_errors, max_error
+from parity import F32_STEP_TOL, F64_TOL, field_errors, floors, max_error
 
 pytestmark = pytest.mark.gpu
 
@@ -50,7 +50,8 @@ CASES = {
     "2d_sod_x_outflow": lambda: I.sod(64, axis=0),
     "2d_sod_y_outflow": lambda: I.sod(64, axis=1),
     "2d_column_nx1": lambda: I.well_balanced_column(40),
-    "2d_walls_n2": lambda: I.stratified_random(2, (5, 2), mu=0.01, kappa=0.01),
+    "2d_walls_n2": lambda: I.stratified_random(2, (5, 2), mu=0.01, kappa=0.01, chi=1.2),
+    "2d_reflect_n2": lambda: I.stratified_random(2, (5, 2), walls=I.REFLECT_HYDRO),
     "3d_periodic_visc": lambda: I.random_periodic(3, (9, 7, 11), seed=3, mu=0.02, kappa=0.03),
     "3d_strat_noslip_visc_ragged": lambda: I.stratified_random(3, (7, 18, 9), mu=0.01, kappa=0.02),
     "3d_strat_reflect": lambda: I.stratified_random(3, (19, 6, 8), walls=I.REFLECT_HYDRO),
@@ -136,12 +137,13 @@ def test_full_size_3d_rb_sampled(precision):
     assert dt == pytest.approx(O.dt(prob, U), rel=1e-14 if precision == "f64" else 1e-6)
     rng = np.random.default_rng(0)
     tol = F64_TOL if precision == "f64" else F32_STEP_TOL
+    fl = floors(prob, U)
     for p in _sample_points(prob, rng, 12):
         lo = [min(p[d], prob.n[d] - 2) for d in range(3)]
         hi = [lo[d] + 2 for d in range(3)]
         W = O.step_window(prob, U, dt, lo, hi)
         sl = (slice(None),) + tuple(slice(lo[d], hi[d]) for d in reversed(range(3)))
-        errs = field_errors(prob, V[sl], W)
+        errs = field_errors(prob, V[sl], W, fl)
         assert max(errs) <= tol, (p, errs)
 
 
