@@ -35,7 +35,7 @@ __global__ void __launch_bounds__(AUX_THREADS) wave_rate_kernel(const __grid_con
 {
     __shared__ double red[AUX_THREADS];
     const int nv = a.n[D - 1];
-    const double dv = a.dx[D - 1];
+    const PhiRow<Real> ph(a);
     const Real gamma = Real(a.gamma), gm1 = Real(a.gamma - 1.0), mu = Real(a.mu), kappa = Real(a.kappa);
     const Real invdx[3] = {Real(1.0 / a.dx[0]), Real(1.0 / a.dx[1]), Real(1.0 / a.dx[2])};
     Real smax = Real(0);
@@ -44,7 +44,7 @@ __global__ void __launch_bounds__(AUX_THREADS) wave_rate_kernel(const __grid_con
         Real b[D + 2];
 #pragma unroll
         for (int k = 0; k < D + 2; ++k) b[k] = __ldg(U + k * a.ncell + idx);
-        const Row<Real> w = row_info<Real, SPLIT>(a, row_of(a, idx), nv, dv);
+        const Row<Real> w = row_info<Real, SPLIT>(a, ph, row_of(a, idx), nv);
         Real p, rho;
         const Real sh = wave_rate<D, Real, SPLIT, VISC>(b, w, gm1, gamma, invdx, mu, kappa, p, rho);
         if (!(sh <= smax)) smax = (sh == sh) ? sh : smax;

@@ -95,16 +95,19 @@ template <>
 __device__ __forceinline__ float rsqrt_<float>(float x) { return rsqrtf(x); }
 
 // Phi at the centre of row r of the gravity axis (Phi = -g x_last), in the
-// state precision (FP32 kernels do no FP64 arithmetic per plane: GB300's FP64
-// rate is 1/64 of its FP32 rate).
+// state precision.  The FP64 form evaluates the oracle's expression; kernels
+// keep (g, lo, dz) as Real constants so that FP32 forms do no FP64 work per
+// plane (GB300's FP64 rate, conversions included, is 1/64 of its FP32 rate).
 template <typename Real>
-__device__ __forceinline__ Real phi_row(const StepArgs& a, int r, double)
-{
-    return -(Real(a.g) * (Real(a.lo_v) + (Real(r) + Real(0.5)) * Real(a.dx[a.dim - 1])));
-}
+struct PhiRow {
+    Real g, lo, dv;
+    __device__ explicit PhiRow(const StepArgs& a)
+        : g(Real(a.g)), lo(Real(a.lo_v)), dv(Real(a.dx[a.dim - 1])) {}
+    __device__ Real operator()(int r) const { return -(g * (lo + (Real(r) + Real(0.5)) * dv)); }
+};
 
 template <typename Real, bool SPLIT>
-__device__ __forceinline__ Row<Real> row_info(const StepArgs& a, int r, int nv, double dv)
+__device__ __forceinline__ Row<Real> row_info(const StepArgs& a, const PhiRow<Real>& ph, int r, int nv)
 {
     Row<Real> w;
     if constexpr (SPLIT) {
@@ -116,7 +119,7 @@ __device__ __forceinline__ Row<Real> row_info(const StepArgs& a, int r, int nv, 
     } else {
         w.rho0 = Real(0); w.p0 = Real(0); w.T0 = Real(0);
     }
-    w.phi = phi_row<Real>(a, r, dv);
+    w.phi = ph(r);
     return w;
 }
 
@@ -228,17 +231,16 @@ struct Stepper {
     const Real* __restrict__ U;
     long long N;
     int nx, ny, nv;
-    double dv;
+    PhiRow<Real> phi;
     Real gm1, gamma;
 
-    __device__ Stepper(const StepArgs& args) : a(args)
+    __device__ Stepper(const StepArgs& args) : a(args), phi(args)
     {
         U = static_cast<const Real*>(a.Uin);
         N = a.ncell;
         nx = a.n[0];
         ny = D == 3 ? a.n[1] : 1;
         nv = a.n[V];
-        dv = a.dx[V];
         gamma = Real(a.gamma);
         gm1 = Real(a.gamma - 1.0);
     }
@@ -297,32 +299,32 @@ struct Stepper {
     // Out of line: only cells of ghost planes and of tiles touching the box edge come here.
     __device__ __noinline__ Cell<D, Real> fetch(int gx, int gy, int gv) const
     {
-        if (gv >= 0 && gv < nv) return fetch_h(gx, gy, gv, row_info<Real, SPLIT>(a, gv, nv, dv));
+        if (gv >= 0 && gv < nv) return fetch_h(gx, gy, gv, row_info<Real, SPLIT>(a, phi, gv, nv));
         const bool lo = gv < 0;
         const int bc = lo ? a.bc_lo[V] : a.bc_hi[V];
         if (bc == BC_PERIODIC) {
             const int s = ((gv % nv) + nv) % nv;
-            return fetch_h(gx, gy, s, row_info<Real, SPLIT>(a, s, nv, dv));
+            return fetch_h(gx, gy, s, row_info<Real, SPLIT>(a, phi, s, nv));
         }
-        const Row<Real> wg = row_info<Real, SPLIT>(a, gv, nv, dv);
+        const Row<Real> wg = row_info<Real, SPLIT>(a, phi, gv, nv);
         if (bc == BC_OUTFLOW) {
             const int s = lo ? 0 : nv - 1;
-            Cell<D, Real> M = fetch_h(gx, gy, s, row_info<Real, SPLIT>(a, s, nv, dv));
+            Cell<D, Real> M = fetch_h(gx, gy, s, row_info<Real, SPLIT>(a, phi, s, nv));
             Cell<D, Real> g = M;   // (rho, u, p) copied; base rows of an outflow ghost copy the edge row
             cons_from_prim<D, Real, SPLIT>(g, wg, gm1, gamma);
             return g;
         }
         const Real Tw = Real(lo ? a.Tw_lo[V] : a.Tw_hi[V]);
         const int r0 = lo ? 0 : nv - 1, r1 = lo ? 1 : nv - 2, g1r = lo ? -1 : nv;
-        const Row<Real> w0 = row_info<Real, SPLIT>(a, r0, nv, dv);
-        const Row<Real> w1g = row_info<Real, SPLIT>(a, g1r, nv, dv);
+        const Row<Real> w0 = row_info<Real, SPLIT>(a, phi, r0, nv);
+        const Row<Real> w1g = row_info<Real, SPLIT>(a, phi, g1r, nv);
         const Cell<D, Real> M0 = fetch_h(gx, gy, r0, w0);
-        const Real dphi1 = phi_row<Real>(a, g1r, dv) - phi_row<Real>(a, r0, dv);
+        const Real dphi1 = phi(g1r) - phi(r0);
         Cell<D, Real> g1 = wall_ghost<D, Real, SPLIT>(M0, M0, bc, V, Tw, w1g, dphi1, gm1, gamma);
         if (gv == g1r) return g1;
-        const Row<Real> w1 = row_info<Real, SPLIT>(a, r1, nv, dv);
+        const Row<Real> w1 = row_info<Real, SPLIT>(a, phi, r1, nv);
         const Cell<D, Real> M1 = fetch_h(gx, gy, r1, w1);
-        const Real dphi2 = phi_row<Real>(a, gv, dv) - phi_row<Real>(a, g1r, dv);
+        const Real dphi2 = phi(gv) - phi(g1r);
         return wall_ghost<D, Real, SPLIT>(M1, g1, bc, V, Tw, wg, dphi2, gm1, gamma);
     }
 };
@@ -491,7 +493,7 @@ ark_step_kernel(const __grid_constant__ StepArgs a)
 
         // ---------------- A: plane f (primitives), prefetch of plane f + 1 ----------------
         const bool fin = f >= 0 && f < nv;
-        const Row<Real> wf = row_info<Real, SPLIT>(a, fin ? f : 0, nv, S.dv);
+        const Row<Real> wf = row_info<Real, SPLIT>(a, S.phi, fin ? f : 0, nv);
 #pragma unroll
         for (int s = 0; s < NSLOT; ++s) {
             const int c = tid + s * NT;
@@ -542,7 +544,7 @@ ark_step_kernel(const __grid_constant__ StepArgs a)
         }
         if (f >= z0 - 1) {
             // faces between planes f-1 (low side) and f (high side), over R1 cells
-            const Real dphi = phi_row<Real>(a, f, S.dv) - phi_row<Real>(a, f - 1, S.dv);
+            const Real dphi = S.phi(f) - S.phi(f - 1);
             const Real r0f = base(B_R0F, f - 1);
             for (int c = tid; c < NR1; c += NT) {
                 const int lx = c % C::R1X - 1, ly = c / C::R1X - C::H1;
@@ -793,7 +795,7 @@ ark_step_kernel(const __grid_constant__ StepArgs a)
 #pragma unroll
                 for (int k = 0; k < NF; ++k) Uo[k * N + idx] = nb[k];
                 // CFL wave rate of U^{n+1} (next step's dt) and physical checks
-                const Row<Real> w = row_info<Real, SPLIT>(a, q, nv, S.dv);
+                const Row<Real> w = row_info<Real, SPLIT>(a, S.phi, q, nv);
                 Real p, rho;
                 const Real sh = wave_rate<D, Real, SPLIT, VISC>(nb, w, S.gm1, S.gamma, invdx, mu, kappa, p, rho);
                 if (!(sh <= smax_t)) smax_t = (sh == sh) ? sh : smax_t;
