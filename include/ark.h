@@ -182,6 +182,28 @@ ark_status ark_state_device_ptr(ark_handle* h, const void** ptr, size_t* bytes);
  * the gravity axis, threads per block and blocks per launch. */
 ark_status ark_launch_shape(const ark_handle* h, int* tx, int* ty, int* planes, int* threads, int* blocks);
 
+/* CFL time step of an FP64 state that the caller keeps on the device, computed
+ * without allocating any device memory and without a handle.  The paper has no
+ * counterpart: this exists for callers that cannot allocate device memory
+ * when they need a time step (a memory pool or arena that owns the device, a
+ * host thread that must not trigger an allocation, which can synchronise the
+ * device or fail when memory is full).
+ *   p   problem description; p->precision must be ARK_F64 (the state is FP64)
+ *   U   device pointer, nf * N FP64 values in the layout above, read only
+ *   dt  device pointer to one double; receives cfl / max wave rate (the
+ *       formula at ark_params.cfl), written on `stream`
+ * Scratch: a fixed array of 16384 doubles (128 KiB) inside the library's
+ * device image, held by every GPU that loads the library until the process
+ * exits; it bounds N to 67,108,864 cells (4096 cells per scratch slot).
+ * Larger grids are rejected with ARK_ERR_INVALID_ARG before any launch.
+ * The first call on a device looks up the array's device address
+ * (cudaGetSymbolAddress) with that device current; make that first call
+ * before any stream capture.  Every call uses the same array and overwrites
+ * the slots it reads, so consecutive calls are independent, but calls that
+ * overlap on the GPU (unordered streams) race on it.  Calls no allocating
+ * routine.  Returns after enqueueing; it does not synchronise. */
+ark_status ark_compute_dt_noalloc(const ark_params* p, const double* U, double* dt, void* stream);
+
 const char* ark_last_error(const ark_handle* h);
 const char* ark_status_string(ark_status s);
 

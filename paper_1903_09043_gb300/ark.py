@@ -90,6 +90,7 @@ _SIGS = {
     "ark_time": (_st, [_H, _dp, _dp]),
     "ark_state_device_ptr": (_st, [_H, ctypes.POINTER(ctypes.c_void_p), ctypes.POINTER(ctypes.c_size_t)]),
     "ark_launch_shape": (_st, [_H, _ip, _ip, _ip, _ip, _ip]),
+    "ark_compute_dt_noalloc": (_st, [ctypes.POINTER(ark_params), ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p]),
     "ark_last_error": (ctypes.c_char_p, [_H]),
     "ark_status_string": (ctypes.c_char_p, [ctypes.c_int]),
 }
@@ -110,6 +111,7 @@ ark_sync = _lib.ark_sync
 ark_time = _lib.ark_time
 ark_state_device_ptr = _lib.ark_state_device_ptr
 ark_launch_shape = _lib.ark_launch_shape
+ark_compute_dt_noalloc = _lib.ark_compute_dt_noalloc
 ark_last_error = _lib.ark_last_error
 ark_status_string = _lib.ark_status_string
 
