@@ -253,6 +253,56 @@ def e2e_path(prob, U, path, args, stream):
             "h2d_bytes_per_step": nbytes / args.steps, "d2h_bytes_per_step": 16 + nbytes / args.steps}
 
 
+def batch_path(args, stream, hbm):
+    """Ensemble of 256 independent 2D Rayleigh-Benard runs (grids 64x32 to 512x256,
+    Ra in [1e3, 1e6], seeded), FP32-split: one launch per step for all runs (CUDA
+    graph replay, autotuned tiles), against the same runs advanced one at a time."""
+    import torch
+    from paper_1903_09043_gb300 import ark, inputs as I
+    runs = I.ensemble(256, seed=5)
+    probs = [p for p, _ in runs]
+    cells = sum(p.ncells for p in probs)
+    b = ark.Batch(probs, "f32split", stream=stream.cuda_stream)
+    for i, (_, U) in enumerate(runs):
+        b.set_state(i, U)
+    tx, planes = b.tune(reps=3)
+    b.step(args.warmup)
+    torch.cuda.synchronize()
+    ev0 = torch.cuda.Event(enable_timing=True)
+    ev1 = torch.cuda.Event(enable_timing=True)
+    ev0.record(stream)
+    b.step(args.steps)
+    ev1.record(stream)
+    torch.cuda.synchronize()
+    ms = ev0.elapsed_time(ev1) / args.steps
+    shape = b.shape()
+    bad = sum(1 for i in range(len(runs)) if b.diagnostics(i, check=False)["status"])
+    b.close()
+    # the same runs, one at a time (one grid, one launch per step, runs in sequence)
+    solvers = []
+    for p, U in runs:
+        s = ark.Solver(p, "f32split", stream=stream.cuda_stream)
+        s.set_state(U)
+        s.step(args.warmup)
+        solvers.append(s)
+    torch.cuda.synchronize()
+    ev0.record(stream)
+    for s in solvers:
+        s.step(args.steps)
+    ev1.record(stream)
+    torch.cuda.synchronize()
+    ms_one = ev0.elapsed_time(ev1) / args.steps
+    for s in solvers:
+        s.close()
+    achieved = cells * ALG_BYTES[("f32split", 2)] / (ms * 1e-3) / 1e9
+    return {"value": cells / (ms * 1e-3), "ms_per_step": ms, "runs": len(runs), "cells": cells, "dtype": "f32",
+            "one_at_a_time_value": cells / (ms_one * 1e-3), "one_at_a_time_ms_per_step": ms_one,
+            "speedup_vs_one_at_a_time": ms_one / ms, "tile": shape, "tuned": {"tx": tx, "planes": planes},
+            "launches_per_step": 1, "runs_with_status": bad,
+            "roofline": {"bound": "hbm", "achieved": achieved, "peak": hbm, "unit": "GB/s", "frac": achieved / hbm,
+                         "alg_bytes_per_cell": ALG_BYTES[("f32split", 2)], "traffic": None}}
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -262,6 +312,7 @@ def main():
     ap.add_argument("--paths", default="f32split,f64")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--no-batch", action="store_true")
     args = ap.parse_args()
     world, rank, local = dist_setup()
     if args.impl == "reference":
@@ -304,6 +355,9 @@ def main():
                            parallelism="replicas" if world > 1 else "single GPU"),
             "roofline": h["roofline"], "clocks": h["clocks"], "gpu_launches": args.steps,
             "paths": {p: {k: v for k, v in r.items() if k != "clocks"} for p, r in results.items()}}
+    if not args.no_batch:
+        with torch.cuda.stream(stream):
+            line["paths"]["batch"] = batch_path(args, stream, hbm)
     if rank == 0 and not args.no_e2e:
         with torch.cuda.stream(stream):
             line["e2e"] = e2e_path(prob, U, head, args, stream)

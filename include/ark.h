@@ -204,6 +204,49 @@ ark_status ark_launch_shape(const ark_handle* h, int* tx, int* ty, int* planes, 
  * routine.  Returns after enqueueing; it does not synchronise. */
 ark_status ark_compute_dt_noalloc(const ark_params* p, const double* U, double* dt, void* stream);
 
+/* ---------------------------------------------------------------------------
+ * Ensembles: many independent 2D runs advanced together, one kernel launch
+ * per step for all of them (not in the paper; an ensemble of its Rayleigh-
+ * Benard set-ups of different sizes and Rayleigh numbers).
+ * ------------------------------------------------------------------------- */
+typedef struct ark_batch ark_batch;
+
+/* Create an ensemble of `count` runs.  params[i] describes run i; every run
+ * must be 2D and share the precision (ARK_F64 or ARK_F32_SPLIT) and whether it
+ * has dissipation (mu or kappa > 0).  Each run gets its own device state,
+ * base state and time-step slots, as with ark_create; work is enqueued on
+ * `cuda_stream`.  Errors as ark_create. */
+ark_status ark_batch_create(int count, const ark_params* params, void* cuda_stream, ark_batch** out);
+
+/* Load or store run i's state (layout and ownership as ark_set_state /
+ * ark_get_state).  All runs must be loaded before the first ark_batch_step;
+ * reloading one run after the ensemble has stepped returns ARK_ERR_INVALID_ARG
+ * at the next ark_batch_step (runs advance in lockstep). */
+ark_status ark_batch_set_state(ark_batch* b, int run, const double* U, int on_device);
+ark_status ark_batch_get_state(ark_batch* b, int run, double* U, int on_device);
+
+/* Autotuner: times the batched kernel for every tile width (64, 128, 256
+ * cells) and planes per work item (16, 32, 64), `reps` launches each, on the
+ * current states without changing them (outputs go to the spare buffers,
+ * time and slots to scratch), and keeps the fastest.  Optional outputs. */
+ark_status ark_batch_tune(ark_batch* b, int reps, int* tx, int* planes);
+
+/* Advance every run nsteps >= 0 steps, each with its own CFL time step.  One
+ * launch per step: a persistent grid (resident blocks x SMs) takes (run, tile,
+ * planes) work items from an atomic counter.  Whole 6-step cycles (ping-pong
+ * buffers x 3 rotating time-step slots) replay one CUDA graph built on first
+ * use.  No host synchronisation. */
+ark_status ark_batch_step(ark_batch* b, int nsteps);
+
+/* Diagnostics of run i (as ark_diagnostics). */
+ark_status ark_batch_diagnostics(ark_batch* b, int run, ark_diag* out);
+
+/* Chosen tile width, planes per item, number of work items and resident blocks. */
+ark_status ark_batch_shape(const ark_batch* b, int* tx, int* planes, int* items, int* blocks);
+
+ark_status ark_batch_destroy(ark_batch* b);
+const char* ark_batch_last_error(const ark_batch* b);
+
 const char* ark_last_error(const ark_handle* h);
 const char* ark_status_string(ark_status s);
 

@@ -91,6 +91,15 @@ _SIGS = {
     "ark_state_device_ptr": (_st, [_H, ctypes.POINTER(ctypes.c_void_p), ctypes.POINTER(ctypes.c_size_t)]),
     "ark_launch_shape": (_st, [_H, _ip, _ip, _ip, _ip, _ip]),
     "ark_compute_dt_noalloc": (_st, [ctypes.POINTER(ark_params), ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p]),
+    "ark_batch_create": (_st, [ctypes.c_int, ctypes.POINTER(ark_params), ctypes.c_void_p, ctypes.POINTER(_H)]),
+    "ark_batch_set_state": (_st, [_H, ctypes.c_int, ctypes.c_void_p, ctypes.c_int]),
+    "ark_batch_get_state": (_st, [_H, ctypes.c_int, ctypes.c_void_p, ctypes.c_int]),
+    "ark_batch_tune": (_st, [_H, ctypes.c_int, _ip, _ip]),
+    "ark_batch_step": (_st, [_H, ctypes.c_int]),
+    "ark_batch_diagnostics": (_st, [_H, ctypes.c_int, ctypes.POINTER(ark_diag)]),
+    "ark_batch_shape": (_st, [_H, _ip, _ip, _ip, _ip]),
+    "ark_batch_destroy": (_st, [_H]),
+    "ark_batch_last_error": (ctypes.c_char_p, [_H]),
     "ark_last_error": (ctypes.c_char_p, [_H]),
     "ark_status_string": (ctypes.c_char_p, [ctypes.c_int]),
 }
@@ -114,6 +123,15 @@ ark_launch_shape = _lib.ark_launch_shape
 ark_compute_dt_noalloc = _lib.ark_compute_dt_noalloc
 ark_last_error = _lib.ark_last_error
 ark_status_string = _lib.ark_status_string
+ark_batch_create = _lib.ark_batch_create
+ark_batch_set_state = _lib.ark_batch_set_state
+ark_batch_get_state = _lib.ark_batch_get_state
+ark_batch_tune = _lib.ark_batch_tune
+ark_batch_step = _lib.ark_batch_step
+ark_batch_diagnostics = _lib.ark_batch_diagnostics
+ark_batch_shape = _lib.ark_batch_shape
+ark_batch_destroy = _lib.ark_batch_destroy
+ark_batch_last_error = _lib.ark_batch_last_error
 
 
 class ArkError(RuntimeError):
@@ -226,6 +244,82 @@ class Solver:
     def close(self) -> None:
         if getattr(self, "h", None):
             ark_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *exc):
+        self.close()
+
+
+def _diag_dict(d: ark_diag) -> dict:
+    return {"mass": d.mass, "mom_x": d.momentum[0], "mom_y": d.momentum[1], "mom_z": d.momentum[2],
+            "energy": d.energy, "kinetic": d.kinetic, "max_speed": d.max_speed,
+            "mean_abs_v_last": d.mean_abs_v_last, "min_rho": d.min_rho, "min_p": d.min_p, "t": d.t,
+            "step": d.step, "dt": d.dt, "status": d.status}
+
+
+class Batch:
+    """An ensemble of independent 2D runs (ark_batch_create ... ark_batch_destroy)."""
+
+    def __init__(self, probs, precision="f32split", stream: Optional[int] = None):
+        self.probs = list(probs)
+        prec = PRECISIONS[precision] if isinstance(precision, str) else int(precision)
+        arr = (ark_params * len(self.probs))(*[params_from_problem(p, prec) for p in self.probs])
+        self._params = arr
+        h = _H()
+        st = ark_batch_create(len(self.probs), arr, ctypes.c_void_p(stream or 0), ctypes.byref(h))
+        if st != ARK_OK:
+            raise ArkError(st, f"ark_batch_create: {ark_status_string(st).decode()}")
+        self.h = h
+
+    def _check(self, st: int, what: str):
+        if st != ARK_OK:
+            raise ArkError(st, f"{what}: {ark_batch_last_error(self.h).decode()}")
+
+    def set_state(self, i: int, U) -> None:
+        addr, dev = _ptr(U)
+        self._check(ark_batch_set_state(self.h, int(i), ctypes.c_void_p(addr), dev), "ark_batch_set_state")
+
+    def get_state(self, i: int, out=None):
+        if out is None:
+            p = self.probs[i]
+            out = np.empty((p.nfields,) + p.shape, dtype=np.float64)
+        addr, dev = _ptr(out)
+        self._check(ark_batch_get_state(self.h, int(i), ctypes.c_void_p(addr), dev), "ark_batch_get_state")
+        return out
+
+    def tune(self, reps: int = 3):
+        tx = ctypes.c_int(0)
+        pl = ctypes.c_int(0)
+        self._check(ark_batch_tune(self.h, int(reps), ctypes.byref(tx), ctypes.byref(pl)), "ark_batch_tune")
+        return tx.value, pl.value
+
+    def step(self, nsteps: int = 1) -> None:
+        self._check(ark_batch_step(self.h, int(nsteps)), "ark_batch_step")
+
+    def diagnostics(self, i: int, check: bool = True) -> dict:
+        d = ark_diag()
+        st = ark_batch_diagnostics(self.h, int(i), ctypes.byref(d))
+        if check:
+            self._check(st, "ark_batch_diagnostics")
+        return _diag_dict(d)
+
+    def shape(self) -> dict:
+        v = [ctypes.c_int(0) for _ in range(4)]
+        self._check(ark_batch_shape(self.h, *[ctypes.byref(x) for x in v]), "ark_batch_shape")
+        return dict(zip(("tx", "planes", "items", "blocks"), [x.value for x in v]))
+
+    def close(self) -> None:
+        if getattr(self, "h", None):
+            ark_batch_destroy(self.h)
             self.h = None
 
     def __del__(self):

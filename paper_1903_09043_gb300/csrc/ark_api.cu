@@ -11,32 +11,7 @@
 #include "../../include/ark.h"
 #include "ark_aux.cuh"
 #include "ark_base.h"
-
-struct ark_handle {
-    ark_params p;
-    int dim = 2, nf = 4, prec = 0, visc = 0;
-    long long N = 0;
-    size_t esz = 8;
-    cudaStream_t stream = nullptr;
-    void* U[2] = {nullptr, nullptr};
-    int cur = 0;
-    void* base = nullptr;          // Real tables [NBASE][nv + 4]
-    double* base64 = nullptr;      // FP64 rho0, p0, W0 [3][nv + 4]
-    void* ctrl = nullptr;          // smax[3] | status | pad | time | dt_last | diag out[16] | partials
-    unsigned long long* smax = nullptr;
-    unsigned int* status = nullptr;
-    double* time = nullptr;
-    double* dt_last = nullptr;
-    double* diag_out = nullptr;
-    double* partials = nullptr;
-    long long step = 0;
-    bool dt_valid = false;
-    bool state_set = false;
-    ark::StepKernelInfo kinfo{};
-    dim3 grid;
-    int planes = 1, tiles_x = 1, tiles_y = 1;
-    std::string err;
-};
+#include "ark_handle.h"
 
 namespace {
 
@@ -57,9 +32,11 @@ ark_status cuda_fail(ark_handle* h, cudaError_t e, const char* where)
         if (e_ != cudaSuccess) return cuda_fail((h), e_, #call);    \
     } while (0)
 
-int nv_of(const ark_handle* h) { return h->p.grid.n[h->dim - 1]; }
+}  // namespace
 
-ark::StepArgs base_args(const ark_handle* h)
+int ark::nv_of(const ark_handle* h) { return h->p.grid.n[h->dim - 1]; }
+
+ark::StepArgs ark::base_args(const ark_handle* h)
 {
     ark::StepArgs a;
     std::memset(&a, 0, sizeof a);
@@ -91,8 +68,14 @@ ark::StepArgs base_args(const ark_handle* h)
     a.status = h->status;
     a.time = h->time;
     a.dt_last = h->dt_last;
+    ark::fill_constants(a);
     return a;
 }
+
+namespace {
+
+using ark::base_args;
+using ark::nv_of;
 
 ark_status validate(const ark_params* p, std::string& msg)
 {
@@ -146,7 +129,9 @@ void choose_launch(ark_handle* h, int nsm)
     h->grid = dim3(tiles, nchunk, 1);
 }
 
-ark_status ensure_dt(ark_handle* h)
+}  // namespace
+
+ark_status ark::ensure_dt(ark_handle* h)
 {
     if (h->dt_valid) return ARK_OK;
     unsigned long long* slot = h->smax + (h->step % 3);
@@ -157,7 +142,7 @@ ark_status ensure_dt(ark_handle* h)
     return ARK_OK;
 }
 
-}  // namespace
+using ark::ensure_dt;
 
 extern "C" {
 

@@ -36,8 +36,9 @@ __global__ void __launch_bounds__(AUX_THREADS) wave_rate_kernel(const __grid_con
     __shared__ double red[AUX_THREADS];
     const int nv = a.n[D - 1];
     const PhiRow<Real> ph(a);
-    const Real gamma = Real(a.gamma), gm1 = Real(a.gamma - 1.0), mu = Real(a.mu), kappa = Real(a.kappa);
-    const Real invdx[3] = {Real(1.0 / a.dx[0]), Real(1.0 / a.dx[1]), Real(1.0 / a.dx[2])};
+    const KConst<Real> kc(a);
+    const Real gamma = kc.gamma, gm1 = kc.gm1, mu = kc.mu, kappa = kc.kappa;
+    const Real invdx[3] = {kc.invdx[0], kc.invdx[1], kc.invdx[2]};
     Real smax = Real(0);
     for (long long idx = blockIdx.x * (long long)blockDim.x + threadIdx.x; idx < a.ncell;
          idx += (long long)gridDim.x * blockDim.x) {

@@ -37,4 +37,12 @@ struct StepKernelInfo {
 StepKernelInfo step_kernel_2d(int prec, int visc);
 StepKernelInfo step_kernel_3d(int prec, int visc);
 
+// Batched 2D step-kernel instances (ark_batch_2d*.cu): tile widths 64, 128, 256.
+struct BatchKernelInfo {
+    const void* func;   // ark_batch_kernel instance (argument list: runs, items, nitems, ctr, ctr_cur, ctr_next)
+    int tx, threads;
+    size_t smem;        // dynamic shared memory per block
+};
+BatchKernelInfo batch_kernel_2d(int prec, int visc, int tx);   // func == nullptr if not built
+
 }  // namespace ark

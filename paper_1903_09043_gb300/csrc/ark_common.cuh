@@ -55,6 +55,32 @@ struct StepArgs {
     unsigned int* status;
     double* time;           // simulated time, advanced by dt each step
     double* dt_last;        // dt of this step
+    // constants of the stencil in both precisions, rounded once on the host, so
+    // that no kernel converts between precisions (conversions run on GB300's
+    // FP64 pipe, 1/64 of its FP32 rate)
+    float fK, fhalfInvK, fmu, fkappa, feta, fgamma, fgm1, fphi_g, fphi_lo, fphi_dv, finvdx[3];
+    double dK, dhalfInvK, deta, dinvdx[3];
 };
+
+// Set the precomputed constants of a StepArgs whose double fields are filled.
+inline void fill_constants(StepArgs& a)
+{
+    const int V = a.dim - 1;
+    a.dK = a.K;
+    a.dhalfInvK = 0.5 / a.K;
+    a.deta = -2.0 / 3.0 * a.mu;
+    for (int d = 0; d < 3; ++d) a.dinvdx[d] = 1.0 / a.dx[d];
+    a.fK = (float)a.K;
+    a.fhalfInvK = (float)a.dhalfInvK;
+    a.fmu = (float)a.mu;
+    a.fkappa = (float)a.kappa;
+    a.feta = (float)a.deta;
+    a.fgamma = (float)a.gamma;
+    a.fgm1 = (float)(a.gamma - 1.0);
+    a.fphi_g = (float)a.g;
+    a.fphi_lo = (float)a.lo_v;
+    a.fphi_dv = (float)a.dx[V];
+    for (int d = 0; d < 3; ++d) a.finvdx[d] = (float)a.dinvdx[d];
+}
 
 }  // namespace ark

@@ -1,0 +1,39 @@
+// ark_handle.h -- the single-grid handle behind include/ark.h (host code).
+#pragma once
+
+#include <string>
+
+#include "../../include/ark.h"
+#include "ark_aux.cuh"
+
+struct ark_handle {
+    ark_params p;
+    int dim = 2, nf = 4, prec = 0, visc = 0;
+    long long N = 0;
+    size_t esz = 8;
+    cudaStream_t stream = nullptr;
+    void* U[2] = {nullptr, nullptr};
+    int cur = 0;
+    void* base = nullptr;          // Real tables [NBASE][nv + 4]
+    double* base64 = nullptr;      // FP64 rho0, p0, W0 [3][nv + 4]
+    void* ctrl = nullptr;          // smax[3] | status | pad | time | dt_last | diag out[16] | partials
+    unsigned long long* smax = nullptr;
+    unsigned int* status = nullptr;
+    double* time = nullptr;
+    double* dt_last = nullptr;
+    double* diag_out = nullptr;
+    double* partials = nullptr;
+    long long step = 0;
+    bool dt_valid = false;
+    bool state_set = false;
+    ark::StepKernelInfo kinfo{};
+    dim3 grid;
+    int planes = 1, tiles_x = 1, tiles_y = 1;
+    std::string err;
+};
+
+namespace ark {
+int nv_of(const ark_handle* h);
+StepArgs base_args(const ark_handle* h);   // every field but Uin/Uout/dt/slots
+ark_status ensure_dt(ark_handle* h);       // wave rate of the current state into slot step % 3
+}  // namespace ark

@@ -61,7 +61,7 @@ struct StepCfg {
     static constexpr int O_TFLUX = O_TL + 2 * (NF + 1) * NR1;          // [NF][NTX + NTY]
     static constexpr int O_VFLUX = O_TFLUX + NF * (NTX + NTY);         // [NV][NTX + NTY]
     static constexpr int N_REAL = O_VFLUX + (VISC ? NV * (NTX + NTY) : 0);
-    static constexpr size_t SMEM_BYTES = ((N_REAL * sizeof(Real) + 15) / 16) * 16 + NT * sizeof(double);
+    static constexpr size_t SMEM_BYTES = ((N_REAL * sizeof(Real) + 15) / 16) * 16 + NT * sizeof(double) + 4 * sizeof(double);
 
     static constexpr int TXV = TX, TYV = TY;
     __device__ static int i2(int lx, int ly) { return (ly + HY) * R2X + (lx + 2); }
@@ -87,12 +87,42 @@ struct Row {
 template <typename Real>
 __device__ __forceinline__ Real rcp(Real x) { return Real(1) / x; }
 
+// Math in the state precision, named explicitly so that no float argument is
+// ever promoted to a double routine (the FP64 pipe is 1/64 of FP32 on GB300).
+__device__ __forceinline__ float vmax(float a, float b) { return fmaxf(a, b); }
+__device__ __forceinline__ double vmax(double a, double b) { return fmax(a, b); }
+__device__ __forceinline__ float vmin(float a, float b) { return fminf(a, b); }
+__device__ __forceinline__ double vmin(double a, double b) { return fmin(a, b); }
+__device__ __forceinline__ float vabs(float a) { return fabsf(a); }
+__device__ __forceinline__ double vabs(double a) { return fabs(a); }
+__device__ __forceinline__ float vsqrt(float a) { return sqrtf(a); }
+__device__ __forceinline__ double vsqrt(double a) { return sqrt(a); }
+
 template <typename Real>
 __device__ __forceinline__ Real rsqrt_(Real x);
 template <>
 __device__ __forceinline__ double rsqrt_<double>(double x) { return rsqrt(x); }
 template <>
 __device__ __forceinline__ float rsqrt_<float>(float x) { return rsqrtf(x); }
+
+// The stencil constants in the state precision, read from the arguments
+// without conversion.
+template <typename Real>
+struct KConst;
+template <>
+struct KConst<float> {
+    float K, halfInvK, mu, kappa, eta, gamma, gm1, invdx[3];
+    __device__ explicit KConst(const StepArgs& a)
+        : K(a.fK), halfInvK(a.fhalfInvK), mu(a.fmu), kappa(a.fkappa), eta(a.feta), gamma(a.fgamma), gm1(a.fgm1),
+          invdx{a.finvdx[0], a.finvdx[1], a.finvdx[2]} {}
+};
+template <>
+struct KConst<double> {
+    double K, halfInvK, mu, kappa, eta, gamma, gm1, invdx[3];
+    __device__ explicit KConst(const StepArgs& a)
+        : K(a.dK), halfInvK(a.dhalfInvK), mu(a.mu), kappa(a.kappa), eta(a.deta), gamma(a.gamma), gm1(a.gamma - 1.0),
+          invdx{a.dinvdx[0], a.dinvdx[1], a.dinvdx[2]} {}
+};
 
 // Phi at the centre of row r of the gravity axis (Phi = -g x_last), in the
 // state precision.  The FP64 form evaluates the oracle's expression; kernels
@@ -102,12 +132,15 @@ template <typename Real>
 struct PhiRow {
     Real g, lo, dv;
     __device__ explicit PhiRow(const StepArgs& a)
-        : g(Real(a.g)), lo(Real(a.lo_v)), dv(Real(a.dx[a.dim - 1])) {}
-    __device__ Real operator()(int r) const { return -(g * (lo + (Real(r) + Real(0.5)) * dv)); }
+        : g(sizeof(Real) == 8 ? Real(a.g) : Real(a.fphi_g)), lo(sizeof(Real) == 8 ? Real(a.lo_v) : Real(a.fphi_lo)),
+          dv(sizeof(Real) == 8 ? Real(a.dx[a.dim - 1]) : Real(a.fphi_dv)) {}
+    __device__ Real operator()(int r) const { return at(Real(r)); }
+    __device__ Real at(Real r) const { return -(g * (lo + (r + Real(0.5)) * dv)); }
 };
 
 template <typename Real, bool SPLIT>
-__device__ __forceinline__ Row<Real> row_info(const StepArgs& a, const PhiRow<Real>& ph, int r, int nv)
+__device__ __forceinline__ Row<Real> row_info(const StepArgs& a, const PhiRow<Real>& ph, int r, int nv,
+                                              Real rf = Real(-1e30))
 {
     Row<Real> w;
     if constexpr (SPLIT) {
@@ -119,7 +152,7 @@ __device__ __forceinline__ Row<Real> row_info(const StepArgs& a, const PhiRow<Re
     } else {
         w.rho0 = Real(0); w.p0 = Real(0); w.T0 = Real(0);
     }
-    w.phi = ph(r);
+    w.phi = rf > Real(-1e29) ? ph.at(rf) : ph(r);   // rf: the row as a Real, when the caller has it
     return w;
 }
 
@@ -139,7 +172,7 @@ __device__ __forceinline__ void prim(Cell<D, Real>& c, const Row<Real>& w, Real 
     c.dp = gm1 * (c.dW - Real(0.5) * ke - c.drho * w.phi);
     const Real p = SPLIT ? w.p0 + c.dp : c.dp;
     c.dT = SPLIT ? (c.dp - w.T0 * c.drho) * rr : p * rr;
-    c.c = sqrt(gamma * p * rr);
+    c.c = vsqrt(gamma * p * rr);
 }
 
 // Conserved values of a ghost built from primitives (rho full, u, dp, dT).
@@ -155,7 +188,7 @@ __device__ __forceinline__ void cons_from_prim(Cell<D, Real>& g, const Row<Real>
     g.dW = g.dp / gm1 + Real(0.5) * ke + g.drho * w.phi;
     const Real p = SPLIT ? w.p0 + g.dp : g.dp;
     g.rr = rcp(g.rho);
-    g.c = sqrt(gamma * p * g.rr);
+    g.c = vsqrt(gamma * p * g.rr);
 }
 
 // Wall ghost (reflective hydrostatic or no-slip fixed-temperature): velocity
@@ -206,16 +239,16 @@ __device__ __forceinline__ Real wave_rate(const Real* b, const Row<Real>& w, Rea
     }
     const Real dp = gm1 * (b[D + 1] - Real(0.5) * ke - b[0] * w.phi);
     p = SPLIT ? w.p0 + dp : dp;
-    const Real cs = sqrt(gamma * p * rr);
+    const Real cs = vsqrt(gamma * p * rr);
 #pragma unroll
-    for (int d = 0; d < D; ++d) sh += (fabs(uu[d]) + cs) * invdx[d];
+    for (int d = 0; d < D; ++d) sh += (vabs(uu[d]) + cs) * invdx[d];
     if constexpr (VISC) {
         const Real nu = Real(4.0 / 3.0) * mu * rr, chi = kappa * gm1 * rr;
-        const Real dm = fmax(nu, chi);
+        const Real dm = vmax(nu, chi);
         Real sp = Real(0);
 #pragma unroll
         for (int d = 0; d < D; ++d) sp += Real(2) * dm * invdx[d] * invdx[d];
-        sh = fmax(sh, sp);
+        sh = vmax(sh, sp);
     }
     return sh;
 }
@@ -241,8 +274,9 @@ struct Stepper {
         nx = a.n[0];
         ny = D == 3 ? a.n[1] : 1;
         nv = a.n[V];
-        gamma = Real(a.gamma);
-        gm1 = Real(a.gamma - 1.0);
+        const KConst<Real> kc(a);
+        gamma = kc.gamma;
+        gm1 = kc.gm1;
     }
 
     __device__ Cell<D, Real> load_in(int gx, int gy, int gv, const Row<Real>& w) const
@@ -339,11 +373,11 @@ __device__ __forceinline__ void acoustic_face(Real uL, Real uR, Real dpL, Real d
                                               Real rzR, Real rcL, Real rcR, Real pjump_base, Real dS, Real K,
                                               Real halfInvK, int low_mach, Real& ustar, Real& dPi)
 {
-    const Real a = K * fmax(zL, zR);
-    const Real inv2a = halfInvK * fmin(rzL, rzR);
+    const Real a = K * vmax(zL, zR);
+    const Real inv2a = halfInvK * vmin(rzL, rzR);
     ustar = Real(0.5) * (uL + uR) - (pjump_base + dpR - dpL - dS) * inv2a;
     Real theta = Real(1);
-    if (low_mach) theta = fmin(fabs(ustar) * fmin(rcL, rcR), Real(1));
+    if (low_mach) theta = vmin(vabs(ustar) * vmin(rcL, rcR), Real(1));
     dPi = Real(0.5) * (dpL + dpR) - Real(0.5) * a * theta * (uR - uL);
 }
 
@@ -384,44 +418,54 @@ __device__ __noinline__ void slow_cell(const Stepper<DIM, Real, SPLIT, VISC, TX,
     store_cell<C, DIM, Real>(x, vT, ff, uc, c, lx, ly);
 }
 
+// One block's share of a step: in-plane tile `tile`, planes [chunk * planes,
+// (chunk + 1) * planes) of the gravity axis.  Called by the single-grid kernel
+// (one block per (tile, chunk)) and by the batched kernel (work items of many runs).
 template <int DIM, typename Real, bool SPLIT, bool VISC, int TX, int TY>
-__global__ void __launch_bounds__(TX * TY, sizeof(Real) == 8 ? 1 : 2)
-ark_step_kernel(const __grid_constant__ StepArgs a)
+__device__ __forceinline__ void step_block(const StepArgs& a, const int tile, const int chunk,
+                                           unsigned char* smem_raw)
 {
     using C = StepCfg<DIM, Real, SPLIT, VISC, TX, TY>;
     constexpr int D = DIM, NF = DIM + 2, V = DIM - 1;
     constexpr int NT = C::NT, NR1 = C::NR1, NR2 = C::NR2, NVT = C::NVT;
     constexpr int NSLOT = (NR2 + NT - 1) / NT;
-    extern __shared__ __align__(16) unsigned char smem_raw[];
     Real* sm = reinterpret_cast<Real*>(smem_raw);
     double* red = reinterpret_cast<double*>(smem_raw + ((C::N_REAL * sizeof(Real) + 15) / 16) * 16);
 
     const Stepper<DIM, Real, SPLIT, VISC, TX, TY> S(a);
     const int tid = threadIdx.x;
-    const int tile = blockIdx.x;
     const int x0 = (tile % a.tiles_x) * TX;
     const int y0 = D == 3 ? (tile / a.tiles_x) * TY : 0;
-    const int z0 = blockIdx.y * a.planes;
+    const int z0 = chunk * a.planes;
     const int z1 = min(z0 + a.planes, S.nv);
     const int nx = S.nx, ny = S.ny, nv = S.nv;
     const Real* __restrict__ U = S.U;
     const long long N = S.N;
 
-    // time step of this step (identical in every block)
-    double dt_d = a.dt_fixed;
-    if (!(dt_d > 0.0)) dt_d = a.cfl / __longlong_as_double((long long)a.smax[a.slot_read]);
-    if (blockIdx.x == 0 && blockIdx.y == 0 && tid == 0) {
-        a.smax[a.slot_reset] = 0ull;
-        *a.time += dt_d;
-        *a.dt_last = dt_d;
+    // time step of this step (identical in every block), formed once by one
+    // thread and shared: nothing FP64 is left for the compiler to recompute
+    Real* const sdt = reinterpret_cast<Real*>(red + NT);
+    if (tid == 0) {
+        double dt_d = a.dt_fixed;
+        if (!(dt_d > 0.0)) dt_d = a.cfl / __longlong_as_double((long long)a.smax[a.slot_read]);
+        if (tile == 0 && chunk == 0) {
+            a.smax[a.slot_reset] = 0ull;
+            *a.time += dt_d;
+            *a.dt_last = dt_d;
+        }
+        sdt[0] = Real(dt_d);
+#pragma unroll
+        for (int d = 0; d < 3; ++d) sdt[1 + d] = d < D ? Real(dt_d * a.dinvdx[d]) : Real(0);
     }
+    __syncthreads();
+    const KConst<Real> kc(a);
     Real lam[3];
 #pragma unroll
-    for (int d = 0; d < 3; ++d) lam[d] = d < D ? Real(dt_d / a.dx[d]) : Real(0);
-    const Real dt = Real(dt_d);
-    const Real K = Real(a.K), halfInvK = Real(0.5 / a.K);
-    const Real mu = Real(a.mu), kappa = Real(a.kappa), eta = Real(-2.0 / 3.0 * a.mu);
-    const Real invdx[3] = {Real(1.0 / a.dx[0]), Real(1.0 / a.dx[1]), Real(1.0 / a.dx[2])};
+    for (int d = 0; d < 3; ++d) lam[d] = sdt[1 + d];
+    const Real dt = sdt[0];
+    const Real K = kc.K, halfInvK = kc.halfInvK;
+    const Real mu = kc.mu, kappa = kc.kappa, eta = kc.eta;
+    const Real invdx[3] = {kc.invdx[0], kc.invdx[1], kc.invdx[2]};
     const Real* __restrict__ Bt = static_cast<const Real*>(a.base);
     const int BL = nv + 4;
     auto base = [&](int field, int r) -> Real { return SPLIT ? __ldg(Bt + field * BL + r + 2) : Real(0); };
@@ -492,8 +536,9 @@ ark_step_kernel(const __grid_constant__ StepArgs a)
         constexpr int TFS = C::NTX + C::NTY;     // component stride of the output-face arrays
 
         // ---------------- A: plane f (primitives), prefetch of plane f + 1 ----------------
+        const Real fr = Real(f);   // plane index as a Real: rows' Phi without further conversions
         const bool fin = f >= 0 && f < nv;
-        const Row<Real> wf = row_info<Real, SPLIT>(a, S.phi, fin ? f : 0, nv);
+        const Row<Real> wf = row_info<Real, SPLIT>(a, S.phi, fin ? f : 0, nv, fin ? fr : Real(0));
 #pragma unroll
         for (int s = 0; s < NSLOT; ++s) {
             const int c = tid + s * NT;
@@ -544,7 +589,7 @@ ark_step_kernel(const __grid_constant__ StepArgs a)
         }
         if (f >= z0 - 1) {
             // faces between planes f-1 (low side) and f (high side), over R1 cells
-            const Real dphi = S.phi(f) - S.phi(f - 1);
+            const Real dphi = S.phi.at(fr) - S.phi.at(fr - Real(1));
             const Real r0f = base(B_R0F, f - 1);
             for (int c = tid; c < NR1; c += NT) {
                 const int lx = c % C::R1X - 1, ly = c / C::R1X - C::H1;
@@ -795,7 +840,7 @@ ark_step_kernel(const __grid_constant__ StepArgs a)
 #pragma unroll
                 for (int k = 0; k < NF; ++k) Uo[k * N + idx] = nb[k];
                 // CFL wave rate of U^{n+1} (next step's dt) and physical checks
-                const Row<Real> w = row_info<Real, SPLIT>(a, S.phi, q, nv);
+                const Row<Real> w = row_info<Real, SPLIT>(a, S.phi, q, nv, fr - Real(2));
                 Real p, rho;
                 const Real sh = wave_rate<D, Real, SPLIT, VISC>(nb, w, S.gm1, S.gamma, invdx, mu, kappa, p, rho);
                 if (!(sh <= smax_t)) smax_t = (sh == sh) ? sh : smax_t;
@@ -826,6 +871,43 @@ ark_step_kernel(const __grid_constant__ StepArgs a)
     }
     if (tid == 0) atomicMax(a.smax + a.slot_write, (unsigned long long)__double_as_longlong(red[0]));
     if (status) atomicOr(a.status, status);
+}
+
+// One launch = one step of one grid: block (x, y) = (in-plane tile, chunk of planes).
+template <int DIM, typename Real, bool SPLIT, bool VISC, int TX, int TY>
+__global__ void __launch_bounds__(TX * TY, sizeof(Real) == 8 ? 1 : 2)
+ark_step_kernel(const __grid_constant__ StepArgs a)
+{
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    step_block<DIM, Real, SPLIT, VISC, TX, TY>(a, blockIdx.x, blockIdx.y, smem_raw);
+}
+
+// Work item of the batched step: one (run, tile, chunk).
+struct BatchItem {
+    int run, tile, chunk, pad;
+};
+
+// One launch = one step of every run of an ensemble.  A fixed grid of blocks
+// (resident blocks per SM x SMs) takes work items from an atomic counter
+// until none is left; item 0's taker resets the counter of the next step.
+// Every run has its own arguments (state pointers, base tables, dt slots).
+template <int DIM, typename Real, bool SPLIT, bool VISC, int TX, int TY>
+__global__ void __launch_bounds__(TX * TY, sizeof(Real) == 8 ? 1 : 512 / (TX * TY))
+ark_batch_kernel(const StepArgs* __restrict__ runs, const BatchItem* __restrict__ items, int nitems, int* ctr,
+                 int ctr_cur, int ctr_next)
+{
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    __shared__ int s_item;
+    for (;;) {
+        __syncthreads();
+        if (threadIdx.x == 0) s_item = atomicAdd(ctr + ctr_cur, 1);
+        __syncthreads();
+        const int it = s_item;
+        if (it >= nitems) break;
+        if (it == 0 && threadIdx.x == 0) ctr[ctr_next] = 0;
+        const BatchItem w = items[it];
+        step_block<DIM, Real, SPLIT, VISC, TX, TY>(runs[w.run], w.tile, w.chunk, smem_raw);
+    }
 }
 
 }  // namespace ark
