@@ -41,9 +41,13 @@ ALG_BYTES = {("f64", 3): 80, ("f32", 3): 40, ("f32split", 3): 40, ("f64", 2): 64
 STEP_KERNEL = "ark_step_kernel"
 
 
-def make_workload():
+# A smaller case of the same set-up (state 160 MB FP32 / 320 MB FP64, still larger
+# than L2) used for ncu captures, which replay each launch many times.
+SMALL = dict(WORKLOAD, workload="rayleigh_benard_3d_256x256x128", n=[256, 256, 128])
+
+
+def make_workload(w=WORKLOAD):
     from paper_1903_09043_gb300 import inputs as I
-    w = WORKLOAD
     return I.rayleigh_benard(3, tuple(w["n"]), m=w["polytrope_m"], chi=w["chi"], Ra=w["Ra"], Pr=w["Pr"],
                              amp=w["perturbation"], seed=w["seed"], low_mach=w["low_mach"], cfl=w["cfl"])
 
@@ -313,6 +317,8 @@ def main():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-batch", action="store_true")
+    ap.add_argument("--workload", default="full", choices=["full", "small"],
+                    help="small: 256x256x128 case of the same set-up, for profiler captures")
     args = ap.parse_args()
     world, rank, local = dist_setup()
     if args.impl == "reference":
@@ -326,7 +332,8 @@ def main():
     else:
         torch.cuda.set_device(0)
     from paper_1903_09043_gb300 import ark  # noqa: F401  (fails loudly without libark.so)
-    prob, U = make_workload()
+    wl = SMALL if args.workload == "small" else WORKLOAD
+    prob, U = make_workload(wl)
     stream = torch.cuda.Stream()
     peaks, peak_kind = measured_peaks()
     hbm = float(peaks.get("hbm_gbs", 6800.0))
@@ -351,7 +358,7 @@ def main():
     line = {"metric": METRIC, "value": h["value"], "unit": UNIT, "n_gpus": world, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": h["ms_per_step"], "higher_is_better": True, "scaling": "weak",
             "vs_baseline": None, "dtype": h["dtype"], "data": "synthetic",
-            "config": dict(WORKLOAD, path=head, l2="inputs (1.3-2.7 GB) exceed L2 (129 MB); no flush",
+            "config": dict(wl, path=head, l2="inputs (1.3-2.7 GB) exceed L2 (129 MB); no flush",
                            parallelism="replicas" if world > 1 else "single GPU"),
             "roofline": h["roofline"], "clocks": h["clocks"], "gpu_launches": args.steps,
             "paths": {p: {k: v for k, v in r.items() if k != "clocks"} for p, r in results.items()}}
@@ -361,7 +368,7 @@ def main():
     if rank == 0 and not args.no_e2e:
         with torch.cuda.stream(stream):
             line["e2e"] = e2e_path(prob, U, head, args, stream)
-    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+    if rank == 0 and world == 1 and not args.no_cpu_baseline and args.workload == "full":
         line["cpu_baseline"] = cpu_baseline(prob, U)
     if world > 1:
         import torch.distributed as dist
