@@ -38,6 +38,7 @@ class _Problem(ctypes.Structure):
         ("bc_hi", ctypes.c_int * 3),
         ("T_lo", ctypes.c_double * 3),
         ("T_hi", ctypes.c_double * 3),
+        ("energy_form", ctypes.c_int),
     ]
 
 
@@ -101,6 +102,7 @@ def _struct(prob) -> _Problem:
     s.K = float(prob.K)
     s.cfl = float(prob.cfl)
     s.low_mach = int(prob.low_mach)
+    s.energy_form = int(getattr(prob, "energy_form", 0))
     return s
 
 

@@ -17,6 +17,9 @@
  *      with b~ upwinded on u*;
  *   5. relaxation step, Sec. 2.1.4: Psi^{n+1} = Phi; the conserved energy
  *      rho*calE is unchanged, so nothing is done to the stored state;
+ *   (Appendix B, energy_form 1: the energy variable is rho E without rho Phi
+ *    and the acoustic step adds dt/dx (uS)_i to it,
+ *    (uS)_i = 1/2 (u*_{i+1/2} S_{i+1/2} + u*_{i-1/2} S_{i-1/2});)
  *   6. first-order dissipative fluxes, Sec. 2.2, evaluated from U^n.
  * Multi-dimensional steps sum every direction's face terms into one L~, one
  * tilde state and one update (unsplit).
@@ -90,7 +93,7 @@ static void to_primitive(const orc_problem* P, cell_t* c)
         c->u[d] = c->m[d] / c->rho;
         ke += 0.5 * c->rho * c->u[d] * c->u[d];
     }
-    double rho_e = c->W - ke - c->rho * c->phi;
+    double rho_e = c->W - ke - (P->energy_form == 0 ? c->rho * c->phi : 0.0);
     c->p = (P->gamma - 1.0) * rho_e;
     c->T = c->p / c->rho;
     c->c = sqrt(P->gamma * c->p / c->rho);
@@ -104,7 +107,7 @@ static void to_conserved(const orc_problem* P, cell_t* c)
         c->m[d] = c->rho * c->u[d];
         ke += 0.5 * c->rho * c->u[d] * c->u[d];
     }
-    c->W = c->p / (P->gamma - 1.0) + ke + c->rho * c->phi;
+    c->W = c->p / (P->gamma - 1.0) + ke + (P->energy_form == 0 ? c->rho * c->phi : 0.0);
     c->T = c->p / c->rho;
     c->c = sqrt(P->gamma * c->p / c->rho);
 }
@@ -339,6 +342,9 @@ int orc_step_window(const orc_problem* P, const double* U, double dt,
                     L += lam[d] * (fp->ustar - fm->ustar);
                     mt[d] += -lam[d] * (fp->Pistar - fm->Pistar) + lam[d] * 0.5 * (fp->S + fm->S);
                     Wt -= lam[d] * (fp->Pistar * fp->ustar - fm->Pistar * fm->ustar);
+                    /* Appendix B: energy source dt/dx (uS)_i of the acoustic step */
+                    if (P->energy_form == 1)
+                        Wt += lam[d] * 0.5 * (fp->ustar * fp->S + fm->ustar * fm->S);
                 }
                 Lt[e] = L;
                 Tl[e].rho = c->rho / L;

@@ -27,6 +27,9 @@ typedef struct {
     int low_mach;       /* 1: theta of Eq. 16; 0: theta = 1                  */
     int bc_lo[3], bc_hi[3];
     double T_lo[3], T_hi[3];  /* wall temperatures for ORC_BC_NOSLIP_FIXED_T */
+    int energy_form;    /* 0: rho*calE = rho e + rho u^2/2 + rho Phi (Eq. 6, the
+                           scheme of Sec. 2); 1: rho E = rho e + rho u^2/2 with
+                           the gravity work as a source (Appendix B) */
 } orc_problem;
 
 int orc_nfields(const orc_problem* P);

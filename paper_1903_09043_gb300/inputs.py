@@ -49,6 +49,7 @@ class Problem:
     bc_hi: Tuple[int, int, int] = (PERIODIC, PERIODIC, PERIODIC)
     T_lo: Tuple[float, float, float] = (0.0, 0.0, 0.0)
     T_hi: Tuple[float, float, float] = (0.0, 0.0, 0.0)
+    energy_form: int = 0           # 0: rho*calE with rho*Phi (Sec. 2); 1: rho E, gravity as a source (Appendix B)
 
     @property
     def nfields(self) -> int:
@@ -93,7 +94,7 @@ def _assemble(prob: Problem, rho: np.ndarray, vel: Sequence[np.ndarray], p: np.n
     for d in range(prob.dim):
         U[1 + d] = rho * vel[d]
         ke += 0.5 * rho * vel[d] * vel[d]
-    U[prob.dim + 1] = p / (prob.gamma - 1.0) + ke + rho * phi
+    U[prob.dim + 1] = p / (prob.gamma - 1.0) + ke + (rho * phi if prob.energy_form == 0 else 0.0)
     return U
 
 
@@ -114,6 +115,18 @@ def hydrostatic_profile(phi: np.ndarray, T: np.ndarray, p0: float) -> Tuple[np.n
         p[j + 1] = (p[j] - 0.5 * rho[j] * dphi) / (1.0 + dphi / (2.0 * T[j + 1]))
         rho[j + 1] = p[j + 1] / T[j + 1]
     return rho, p
+
+
+def to_energy_form(prob: Problem, U: np.ndarray, form: int) -> Tuple[Problem, np.ndarray]:
+    """The same physical state with the energy variable of ``form`` (adds or
+    removes rho*Phi; no step arithmetic)."""
+    V = np.array(U, dtype=np.float64, copy=True)
+    phi = -prob.g * _last_axis_centers(prob)
+    if prob.energy_form == 0 and form == 1:
+        V[prob.dim + 1] -= V[0] * phi
+    elif prob.energy_form == 1 and form == 0:
+        V[prob.dim + 1] += V[0] * phi
+    return prob.replace(energy_form=form), V
 
 
 def _bcast_profile(prob: Problem, prof: np.ndarray) -> np.ndarray:

@@ -459,3 +459,45 @@ def test_low_mach_theta_never_exceeds_either_side_mach_number():
             assert f["theta"] <= abs(f["ustar"]) / c * (1 + 1e-14)
         cmax = max(math.sqrt(1.4 * L[4] / L[0]), math.sqrt(1.4 * R[4] / R[0]))
         assert f["theta"] == pytest.approx(min(abs(f["ustar"]) / cmax, 1.0), rel=1e-14)
+
+
+# --------------------------------------------------------------------------
+# Appendix B: non-conservative energy form (rho E without rho Phi, gravity
+# work as the source dt/dx (uS)_i)
+# --------------------------------------------------------------------------
+def test_appendix_b_equals_sec2_scheme_without_gravity():
+    """With a constant potential both energy forms are the same scheme (S = 0)."""
+    prob, U = I.random_periodic(2, (20, 16), mu=0.01, kappa=0.01)
+    p1, U1 = I.to_energy_form(prob, U, 1)
+    A, _ = O.run(prob, U, 20)
+    B, _ = O.run(p1, U1, 20)
+    assert np.array_equal(A, B)
+
+
+def test_appendix_b_keeps_atmosphere_at_rest():
+    prob, U = I.atmosphere((64, 64))
+    p1, U1 = I.to_energy_form(prob, U, 1)
+    V, _ = O.run(p1, U1, 500)
+    assert O.diagnostics(p1, V)["max_speed"] < 1e-13
+
+
+def test_appendix_b_converges_to_the_conservative_form():
+    """Both forms discretise the same equations: on a smooth stratified flow
+    their difference shrinks at first order with the grid (a wrong sign or
+    factor in the (uS) source leaves an O(1) gap)."""
+    gaps = []
+    for n in (16, 32, 64):
+        prob, Ub = I.stratified_random(2, (n, n), seed=3, amp=0.0)
+        x = prob.centers(0)[None, :]
+        y = prob.centers(1)[:, None]
+        pert = 0.05 * np.sin(2 * np.pi * x) * np.sin(np.pi * y)
+        U = Ub.copy()
+        U[2] = Ub[0] * pert
+        U[3] = Ub[3] + 0.5 * Ub[0] * pert ** 2
+        p1, U1 = I.to_energy_form(prob, U, 1)
+        A, _ = O.run(prob, U, 10 ** 6, t_end=0.2)
+        B, _ = O.run(p1, U1, 10 ** 6, t_end=0.2)
+        _, B0 = I.to_energy_form(p1, B, 0)
+        gaps.append(max(np.max(np.abs(A[f] - B0[f])) / np.max(np.abs(A[f])) for f in (0, 2, 3)))
+    assert gaps[0] < 0.02
+    assert math.log2(gaps[0] / gaps[1]) > 0.8 and math.log2(gaps[1] / gaps[2]) > 0.8
