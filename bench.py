@@ -39,6 +39,16 @@ WORKLOAD = {"workload": "rayleigh_benard_3d_512x512x256", "dim": 3, "n": [512, 5
 # algorithmic HBM bytes per cell-update: every conserved field read once and written once
 ALG_BYTES = {("f64", 3): 80, ("f32", 3): 40, ("f32split", 3): 40, ("f64", 2): 64, ("f32", 2): 32, ("f32split", 2): 32}
 STEP_KERNEL = "ark_step_kernel"
+# algorithmic floating-point operations per cell-update of the scheme (each add,
+# sub, mul, div, sqrt, abs, min, max counted once; every face computed once and
+# shared by its two cells): primitives, acoustic faces, tilde state, upwind
+# transport, viscous and heat fluxes, CFL wave rate.  Per-row counts are
+# tabulated with the kernel descriptions in the design notes.
+ALG_FLOPS = {(3, True): 392, (3, False): 213, (2, True): 225, (2, False): 144}
+# ALU peaks from unit counts and the maximum SM clock: 152 SMs x 128 FP32 lanes
+# x 2 (FMA) x 2.07 GHz; FP64: 152 SMs x 2 FP64 FMA per clock x 2 x 2.07 GHz.
+SMS, SM_GHZ = 152, 2.07
+ALU_PEAK_TFLOPS = {"f32": SMS * 128 * 2 * SM_GHZ / 1e3, "f64": SMS * 2 * 2 * SM_GHZ / 1e3}
 
 
 # A smaller case of the same set-up (state 160 MB FP32 / 320 MB FP64, still larger
@@ -348,10 +358,17 @@ def main():
         B = ALG_BYTES[(path, 3)]
         achieved = cells * B / (ms * 1e-3) / 1e9
         traffic = kernel_traffic(path)
+        dt_kind = "f64" if path == "f64" else "f32"
+        flops = ALG_FLOPS[(3, prob.mu > 0 or prob.kappa > 0)]
+        tflops = cells * flops / (ms * 1e-3) / 1e12
+        alu_peak = ALU_PEAK_TFLOPS[dt_kind]
         results[path] = {
-            "value": cells * world / (ms_max * 1e-3), "ms_per_step": ms_max, "dtype": "f64" if path == "f64" else "f32",
-            "roofline": {"bound": "hbm", "achieved": achieved, "peak": hbm, "unit": "GB/s", "frac": achieved / hbm,
-                         "traffic": traffic, "alg_bytes_per_cell": B, "peak_kind": f"{peak_kind} hbm_gbs (burst copy)"},
+            "value": cells * world / (ms_max * 1e-3), "ms_per_step": ms_max, "dtype": dt_kind,
+            "roofline": {"bound": "alu", "achieved": tflops, "peak": alu_peak, "unit": "TFLOP/s",
+                         "frac": tflops / alu_peak, "traffic": traffic, "alg_flops_per_cell": flops,
+                         "peak_kind": f"{dt_kind.upper()} peak from unit counts and the maximum SM clock",
+                         "hbm": {"achieved": achieved, "peak": hbm, "unit": "GB/s", "frac": achieved / hbm,
+                                 "alg_bytes_per_cell": B, "peak_kind": f"{peak_kind} hbm_gbs (burst copy)"}},
             "launch": shape, "final_t": d["t"], "final_dt": d["dt"], "status": d["status"], "clocks": clocks,
         }
     h = results[head]

@@ -107,12 +107,18 @@ typedef struct {
                                   / dx_d^2)                                           */
     ark_bc bc;
     int precision;             /* ARK_F64, ARK_F32 or ARK_F32_SPLIT                   */
+    int energy_form;           /* 0: the energy field is rho*calE = rho e + rho |u|^2/2
+                                  + rho Phi, conserved (Sec. 2); 1: it is rho E = rho e
+                                  + rho |u|^2/2 and the acoustic step adds the gravity
+                                  work dt/dx (uS)_i (Appendix B, not conservative for
+                                  the total energy).  ARK_F32_SPLIT needs 0.           */
 } ark_params;
 
 typedef struct {
     double mass;               /* sum rho dV                                          */
     double momentum[3];        /* sum m dV                                            */
-    double energy;             /* sum rho*calE dV                                     */
+    double energy;             /* sum of the energy field dV (rho*calE, or rho E when
+                                  energy_form == 1)                                    */
     double kinetic;            /* sum rho |u|^2 / 2 dV                                */
     double max_speed;          /* max |u|                                             */
     double mean_abs_v_last;    /* mean |u_last| (vertical velocity)                   */

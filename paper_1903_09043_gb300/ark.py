@@ -63,7 +63,8 @@ class ark_bc(ctypes.Structure):
 class ark_params(ctypes.Structure):
     _fields_ = [("grid", ark_grid), ("eos", ark_eos), ("gravity", ark_gravity), ("mu", ctypes.c_double),
                 ("kappa", ctypes.c_double), ("low_mach", ctypes.c_int), ("K", ctypes.c_double),
-                ("cfl", ctypes.c_double), ("bc", ark_bc), ("precision", ctypes.c_int)]
+                ("cfl", ctypes.c_double), ("bc", ark_bc), ("precision", ctypes.c_int),
+                ("energy_form", ctypes.c_int)]
 
 
 class ark_diag(ctypes.Structure):
@@ -159,6 +160,7 @@ def params_from_problem(prob, precision: int = ARK_F64) -> ark_params:
     p.K = float(prob.K)
     p.cfl = float(prob.cfl)
     p.precision = int(precision)
+    p.energy_form = int(getattr(prob, "energy_form", 0))
     return p
 
 

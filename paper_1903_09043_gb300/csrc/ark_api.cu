@@ -58,6 +58,7 @@ ark::StepArgs ark::base_args(const ark_handle* h)
     a.K = p.K;
     a.cfl = p.cfl;
     a.low_mach = p.low_mach;
+    a.energy_form = p.energy_form;
     a.planes = h->planes;
     a.tiles_x = h->tiles_x;
     a.tiles_y = h->tiles_y;
@@ -107,6 +108,11 @@ ark_status validate(const ark_params* p, std::string& msg)
     if (!(p->mu >= 0.0) || !(p->kappa >= 0.0)) { msg = "mu and kappa must be >= 0"; return ARK_ERR_INVALID_ARG; }
     if (p->precision < ARK_F64 || p->precision > ARK_F32_SPLIT) { msg = "unknown precision"; return ARK_ERR_INVALID_ARG; }
     if (p->low_mach != 0 && p->low_mach != 1) { msg = "low_mach must be 0 or 1"; return ARK_ERR_INVALID_ARG; }
+    if (p->energy_form != 0 && p->energy_form != 1) { msg = "energy_form must be 0 or 1"; return ARK_ERR_INVALID_ARG; }
+    if (p->energy_form == 1 && p->precision == ARK_F32_SPLIT) {
+        msg = "ARK_F32_SPLIT needs energy_form 0 (its base state carries rho Phi)";
+        return ARK_ERR_UNSUPPORTED;
+    }
     return ARK_OK;
 }
 

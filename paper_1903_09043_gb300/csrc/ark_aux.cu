@@ -148,7 +148,7 @@ __global__ void __launch_bounds__(AUX_THREADS) diag_kernel(const StepArgs a, con
     for (long long idx = blockIdx.x * (long long)blockDim.x + threadIdx.x; idx < a.ncell;
          idx += (long long)gridDim.x * blockDim.x) {
         const int r = row_of(a, idx);
-        const double phi = -(a.g * (a.lo_v + (r + 0.5) * a.dx[D - 1]));
+        const double phi = a.energy_form ? 0.0 : -(a.g * (a.lo_v + (r + 0.5) * a.dx[D - 1]));
         double rho = double(U[idx]), W = double(U[(D + 1) * a.ncell + idx]);
         if constexpr (SPLIT) {
             rho += a.base64[0 * (nv + 4) + r + 2];

@@ -43,6 +43,6 @@ struct BatchKernelInfo {
     int tx, threads;
     size_t smem;        // dynamic shared memory per block
 };
-BatchKernelInfo batch_kernel_2d(int prec, int visc, int tx);   // func == nullptr if not built
+BatchKernelInfo batch_kernel_2d(int prec, int visc, int width);   // width: 64, 128, 256 threads per row; func == nullptr if not built
 
 }  // namespace ark

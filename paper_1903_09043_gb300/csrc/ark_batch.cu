@@ -14,7 +14,7 @@ struct ark_batch {
     std::vector<ark_handle*> runs;
     int nsm = 152;
     // launch configuration
-    int tx = 0, planes = 0;
+    int tx = 0, width = 0, planes = 0;   // output tile width, kernel row width, planes per item
     ark::BatchKernelInfo kinfo{};
     int blocks = 0, nitems = 0;
     ark::StepArgs* d_args = nullptr;   // [6 phases][count]
@@ -46,12 +46,14 @@ void drop_graph(ark_batch* b)
     b->graph = nullptr;
 }
 
-// Work items and per-phase argument arrays for tile width tx and `planes`
-// planes per item.  Phase p (= step % 6): input buffer p % 2, output the
-// other, time-step slots read p % 3, write (p + 1) % 3, reset (p + 2) % 3.
-ark_status configure(ark_batch* b, int tx, int planes)
+// Work items and per-phase argument arrays for the kernel instance of row
+// width `width` (its output tile width is kinfo.tx) and `planes` planes per
+// item.  Phase p (= step % 6): input buffer p % 2, output the other,
+// time-step slots read p % 3, write (p + 1) % 3, reset (p + 2) % 3.
+ark_status configure(ark_batch* b, int width, int planes)
 {
-    ark::BatchKernelInfo k = ark::batch_kernel_2d(b->prec, b->visc, tx);
+    ark::BatchKernelInfo k = ark::batch_kernel_2d(b->prec, b->visc, width);
+    const int tx = k.tx;
     if (!k.func) return bfail(b, ARK_ERR_UNSUPPORTED, "no batched kernel for this precision / tile width");
     BCUDA(b, cudaFuncSetAttribute(k.func, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)k.smem));
     int per_sm = 0;
@@ -93,6 +95,7 @@ ark_status configure(ark_batch* b, int tx, int planes)
     BCUDA(b, cudaStreamSynchronize(b->stream));   // host vectors leave scope
     b->kinfo = k;
     b->tx = tx;
+    b->width = width;
     b->planes = planes;
     b->nitems = (int)items.size();
     b->blocks = per_sm * b->nsm;
@@ -299,7 +302,7 @@ ark_status ark_batch_tune(ark_batch* b, int reps, int* tx_out, int* planes_out)
     if (st != ARK_OK) return st;
     st = configure(b, btx, bpl);   // rebuilds the real argument arrays
     if (st != ARK_OK) return st;
-    if (tx_out) *tx_out = btx;
+    if (tx_out) *tx_out = b->tx;
     if (planes_out) *planes_out = bpl;
     return ARK_OK;
 }

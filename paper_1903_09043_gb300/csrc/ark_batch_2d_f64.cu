@@ -3,11 +3,11 @@
 
 namespace ark {
 
-BatchKernelInfo batch_kernel_2d_f64(int visc, int tx)
+BatchKernelInfo batch_kernel_2d_f64(int visc, int width)
 {
-    if (tx == 64) return visc ? batch_info<double, false, true, 64>() : batch_info<double, false, false, 64>();
-    if (tx == 128) return visc ? batch_info<double, false, true, 128>() : batch_info<double, false, false, 128>();
-    if (tx == 256) return visc ? batch_info<double, false, true, 256>() : batch_info<double, false, false, 256>();
+    if (width == 64) return visc ? batch_info<double, false, true, 64>() : batch_info<double, false, false, 64>();
+    if (width == 128) return visc ? batch_info<double, false, true, 128>() : batch_info<double, false, false, 128>();
+    if (width == 256) return visc ? batch_info<double, false, true, 256>() : batch_info<double, false, false, 256>();
     return BatchKernelInfo{nullptr, 0, 0, 0};
 }
 

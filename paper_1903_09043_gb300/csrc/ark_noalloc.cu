@@ -125,6 +125,7 @@ extern "C" ark_status ark_compute_dt_noalloc(const ark_params* p, const double* 
     a.mu = p->mu;
     a.kappa = p->kappa;
     a.cfl = p->cfl;
+    a.energy_form = p->energy_form;
     a.ncell = ncell;
 
     double* scratch = nullptr;

@@ -77,6 +77,7 @@ struct Cell {
     Real drho, m[D], dW;            // conserved values (deviation form in F32_SPLIT)
     Real rho, u[D], dp, dT, c;      // full rho, velocity, deviation p and T (full in F64/F32), c
     Real rr;                        // 1 / rho
+    Real rc;                        // 1 / c
 };
 
 template <typename Real>
@@ -84,8 +85,23 @@ struct Row {
     Real rho0, p0, T0, phi;
 };
 
-template <typename Real>
-__device__ __forceinline__ Real rcp(Real x) { return Real(1) / x; }
+// Reciprocal and square root.  FP64: the exact (correctly rounded) operations,
+// as the oracle uses.  FP32: the hardware approximations (within 2 ulp), one
+// special-function instruction each instead of the IEEE refinement sequences;
+// the FP32 forms' error budget is several ulp per step.
+__device__ __forceinline__ double rcp(double x) { return 1.0 / x; }
+__device__ __forceinline__ float rcp(float x) { return __fdividef(1.0f, x); }
+// c = sqrt(q) and 1 / c together
+__device__ __forceinline__ void sqrt_rsqrt(double q, double& c, double& rc)
+{
+    c = sqrt(q);
+    rc = 1.0 / c;
+}
+__device__ __forceinline__ void sqrt_rsqrt(float q, float& c, float& rc)
+{
+    rc = rsqrtf(q);
+    c = q * rc;
+}
 
 // Math in the state precision, named explicitly so that no float argument is
 // ever promoted to a double routine (the FP64 pipe is 1/64 of FP32 on GB300).
@@ -153,6 +169,7 @@ __device__ __forceinline__ Row<Real> row_info(const StepArgs& a, const PhiRow<Re
         w.rho0 = Real(0); w.p0 = Real(0); w.T0 = Real(0);
     }
     w.phi = rf > Real(-1e29) ? ph.at(rf) : ph(r);   // rf: the row as a Real, when the caller has it
+    if (a.energy_form) w.phi = Real(0);              // rho E carries no potential energy (Appendix B)
     return w;
 }
 
@@ -172,7 +189,7 @@ __device__ __forceinline__ void prim(Cell<D, Real>& c, const Row<Real>& w, Real 
     c.dp = gm1 * (c.dW - Real(0.5) * ke - c.drho * w.phi);
     const Real p = SPLIT ? w.p0 + c.dp : c.dp;
     c.dT = SPLIT ? (c.dp - w.T0 * c.drho) * rr : p * rr;
-    c.c = vsqrt(gamma * p * rr);
+    sqrt_rsqrt(gamma * p * rr, c.c, c.rc);
 }
 
 // Conserved values of a ghost built from primitives (rho full, u, dp, dT).
@@ -188,7 +205,7 @@ __device__ __forceinline__ void cons_from_prim(Cell<D, Real>& g, const Row<Real>
     g.dW = g.dp / gm1 + Real(0.5) * ke + g.drho * w.phi;
     const Real p = SPLIT ? w.p0 + g.dp : g.dp;
     g.rr = rcp(g.rho);
-    g.c = vsqrt(gamma * p * g.rr);
+    sqrt_rsqrt(gamma * p * g.rr, g.c, g.rc);
 }
 
 // Wall ghost (reflective hydrostatic or no-slip fixed-temperature): velocity
@@ -239,7 +256,8 @@ __device__ __forceinline__ Real wave_rate(const Real* b, const Row<Real>& w, Rea
     }
     const Real dp = gm1 * (b[D + 1] - Real(0.5) * ke - b[0] * w.phi);
     p = SPLIT ? w.p0 + dp : dp;
-    const Real cs = vsqrt(gamma * p * rr);
+    Real cs, rcs;
+    sqrt_rsqrt(gamma * p * rr, cs, rcs);
 #pragma unroll
     for (int d = 0; d < D; ++d) sh += (vabs(uu[d]) + cs) * invdx[d];
     if constexpr (VISC) {
@@ -393,7 +411,7 @@ __device__ __forceinline__ void store_cell(const Cell<D, Real>& x, Real* vT, Rea
 #pragma unroll
     for (int d = 0; d < D; ++d) vT[d * C::NR2 + c] = x.u[d];
     if constexpr (C::NVT > D) vT[D * C::NR2 + c] = x.dT;
-    const Real rc = rcp(x.c);
+    const Real rc = x.rc;
     ff[0 * C::NR2 + c] = x.dp;
     ff[1 * C::NR2 + c] = rc;
     ff[2 * C::NR2 + c] = x.rho * x.c;
@@ -636,6 +654,7 @@ __device__ __forceinline__ void step_block(const StepArgs& a, const int tile, co
                 if constexpr (SPLIT) m_t[V] -= lam[V] * Q0;
                 W_t -= lam[V] * (piz_p * usz_p - piz_m * usz_m);
                 if constexpr (SPLIT) W_t -= lam[V] * (dPp * usz_p - dPm * usz_m) + H0 * ell;
+                if (a.energy_form) W_t += lam[V] * Real(0.5) * (usz_p * dSz_p + usz_m * dSz_m);   // (uS)_i, Appendix B
                 const Real L = Real(1) + ell;
                 const Real rL = rcp(L);
                 tl_f1[c] = SPLIT ? (uc_f1[c] - rho0 * ell) * rL : uc_f1[c] * rL;

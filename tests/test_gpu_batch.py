@@ -68,7 +68,7 @@ def test_tuning_leaves_states_unchanged_and_picks_a_shape():
             b.set_state(i, U)
         before = [b.get_state(i) for i in range(len(runs))]
         tx, planes = b.tune(reps=2)
-        assert tx in (64, 128, 256) and planes in (16, 32, 64)
+        assert tx in (60, 124, 252, 64, 128, 256) and planes in (16, 32, 64)
         assert b.shape()["tx"] == tx
         for i in range(len(runs)):
             assert np.array_equal(b.get_state(i), before[i])

@@ -159,6 +159,37 @@ def test_fp32_forms_match_oracle_within_budget(case, precision):
     assert d["status"] == 0
 
 
+APPENDIX_B_CASES = ["2d_atmosphere_ragged", "2d_strat_noslip_visc", "2d_three_tiles", "3d_strat_reflect",
+                    "3d_multi_tile", "3d_rb"]
+
+
+@pytest.mark.parametrize("case", APPENDIX_B_CASES)
+@pytest.mark.parametrize("precision", ["f64", "f32"])
+def test_appendix_b_energy_form_matches_oracle(case, precision):
+    """Energy variable rho E with the gravity work as an acoustic-step source
+    (Appendix B), against the oracle's form of the same."""
+    prob, U = I.to_energy_form(*CASES[case](), 1)
+    n = 20
+    ref, t_ref, dts = O.run(prob, U, n, return_dt=True)
+    V, d = gpu_run(prob, U, n, precision=precision)
+    errs = field_errors(prob, V, ref)
+    assert max(errs) <= (F64_TOL if precision == "f64" else n * F32_STEP_TOL), errs
+    assert d["status"] == 0
+    if precision == "f64":
+        assert d["t"] == pytest.approx(t_ref, rel=1e-13)
+        assert d["dt"] == pytest.approx(dts[-1], rel=1e-13)
+
+
+def test_appendix_b_energy_form_is_rejected_by_split():
+    """The split form's FP64 base state carries rho*Phi in its energy, so it
+    accepts only the conservative energy variable."""
+    ark = _ark()
+    prob, _ = I.to_energy_form(*I.atmosphere((16, 16)), 1)
+    with pytest.raises(ark.ArkError) as ei:
+        ark.Solver(prob, "f32split", stream=_stream())
+    assert ei.value.status == ark.ARK_ERR_UNSUPPORTED
+
+
 def test_split_keeps_atmosphere_at_rest_and_beats_plain_fp32():
     """The FP64 base state makes the FP32 form well balanced: the atmosphere at
     rest stays at rest to FP32 round-off of the deviations, far below plain FP32."""
