@@ -135,7 +135,8 @@ typedef struct ark_handle ark_handle;
 /* Create a solver for one grid.  Validates p (dims, sizes >= 1, n >= 2 along
  * wall/outflow axes, gamma > 1, K >= 1, cfl > 0, mu, kappa >= 0, periodic
  * axes without gravity; ARK_F32_SPLIT: fixed-temperature walls only at the
- * two ends of the gravity axis), allocates the device state (two ping-pong copies of nf * N
+ * two ends of the gravity axis and energy_form 0; ARK_F32 and ARK_F32_SPLIT:
+ * fewer than 2^32 cells, else ARK_ERR_UNSUPPORTED), allocates the device state (two ping-pong copies of nf * N
  * values of the chosen precision) and small scratch on the current device.
  * The state is undefined until ark_set_state.  *out receives the handle,
  * which the caller releases with ark_destroy.

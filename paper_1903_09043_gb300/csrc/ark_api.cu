@@ -113,6 +113,14 @@ ark_status validate(const ark_params* p, std::string& msg)
         msg = "ARK_F32_SPLIT needs energy_form 0 (its base state carries rho Phi)";
         return ARK_ERR_UNSUPPORTED;
     }
+    if (p->precision != ARK_F64) {
+        unsigned long long cells = 1;
+        for (int d = 0; d < dim; ++d) cells *= (unsigned long long)p->grid.n[d];
+        if (cells >= (1ull << 32)) {   // the FP32 kernels index a field with 32-bit offsets
+            msg = "the FP32 forms take fewer than 2^32 cells";
+            return ARK_ERR_UNSUPPORTED;
+        }
+    }
     return ARK_OK;
 }
 
@@ -197,7 +205,7 @@ ark_status ark_create(const ark_params* p, void* cuda_stream, ark_handle** out)
     const size_t ctrl_bytes = 64 + 64 + 16 * 8 + (size_t)ark::DIAG_BLOCKS * ark::DG_NTOT * 8;
     if (cudaMalloc(&h->U[0], bytes) != cudaSuccess || cudaMalloc(&h->U[1], bytes) != cudaSuccess ||
         cudaMalloc(&h->ctrl, ctrl_bytes) != cudaSuccess ||
-        (h->prec == ARK_F32_SPLIT && (cudaMalloc(&h->base, (size_t)ark::NBASE * L * sizeof(float)) != cudaSuccess ||
+        (h->prec == ARK_F32_SPLIT && (cudaMalloc(&h->base, (size_t)ark::BSTRIDE * L * sizeof(float)) != cudaSuccess ||
                                       cudaMalloc((void**)&h->base64, 3 * (size_t)L * sizeof(double)) != cudaSuccess))) {
         cudaGetLastError();
         ark_destroy(h);

@@ -57,8 +57,8 @@ inline void build_base_tables(const BaseSpec& s, const std::vector<double>& rho_
         b64[1 * L + i] = pr[i];
         b64[2 * L + i] = W0[i];
     }
-    std::vector<double> t(NBASE * (size_t)L, 0.0);
-    auto at = [&](int f, int i) -> double& { return t[(size_t)f * L + i]; };
+    std::vector<double> t((size_t)BSTRIDE * L, 0.0);
+    auto at = [&](int f, int i) -> double& { return t[(size_t)i * BSTRIDE + f]; };   // i = r + 2
     for (int i = 0; i < L; ++i) {
         at(B_RHO0, i) = rho[i];
         at(B_P0, i) = pr[i];

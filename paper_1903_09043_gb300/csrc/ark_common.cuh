@@ -10,9 +10,11 @@ enum BC : int { BC_PERIODIC = 0, BC_REFLECT = 1, BC_NOSLIP_T = 2, BC_OUTFLOW = 3
 enum Prec : int { P_F64 = 0, P_F32 = 1, P_F32_SPLIT = 2 };
 enum Status : unsigned { ST_NONPHYS = 1u, ST_LTILDE = 2u, ST_NAN = 4u };
 
-// Per-row base-state table (F32_SPLIT only), rows r = -2 .. nv + 1 stored at
-// index r + 2 of each of the NBASE arrays (each nv + 4 long).  Every entry is
-// formed in FP64 on the host and rounded once to the state precision.
+// Per-row base-state table (F32_SPLIT only), rows r = -2 .. nv + 1, row-major:
+// row r holds its BSTRIDE entries at [(r + 2) * BSTRIDE, (r + 3) * BSTRIDE),
+// in the order of BaseField, grouped by four so that a kernel reads a row's
+// values with 16-byte loads.  Every entry is formed in FP64 on the host and
+// rounded once to the state precision.
 enum BaseField : int {
     B_RHO0 = 0,  // rho0_r
     B_P0,        // p0_r
@@ -29,6 +31,9 @@ enum BaseField : int {
     B_DQ0,       // kappa [(T0_{r+1} - T0_r) - (T0_r - T0_{r-1})] / dz^2: base heat divergence
     NBASE
 };
+constexpr int BSTRIDE = 16;   // entries per row (NBASE rounded up to a multiple of 4)
+static_assert(NBASE <= BSTRIDE, "base row too long");
+__host__ __device__ constexpr int base_index(int field, int r) { return (r + 2) * BSTRIDE + field; }
 
 // Everything one step launch needs, passed by value.
 struct StepArgs {

@@ -14,7 +14,7 @@ struct ark_handle {
     cudaStream_t stream = nullptr;
     void* U[2] = {nullptr, nullptr};
     int cur = 0;
-    void* base = nullptr;          // Real tables [NBASE][nv + 4]
+    void* base = nullptr;          // Real table [nv + 4][BSTRIDE], row-major
     double* base64 = nullptr;      // FP64 rho0, p0, W0 [3][nv + 4]
     void* ctrl = nullptr;          // smax[3] | status | pad | time | dt_last | diag out[16] | partials
     unsigned long long* smax = nullptr;

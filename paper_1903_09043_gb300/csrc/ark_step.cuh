@@ -160,11 +160,10 @@ __device__ __forceinline__ Row<Real> row_info(const StepArgs& a, const PhiRow<Re
 {
     Row<Real> w;
     if constexpr (SPLIT) {
-        const Real* B = static_cast<const Real*>(a.base);
-        const int L = nv + 4;
-        w.rho0 = __ldg(B + B_RHO0 * L + r + 2);
-        w.p0 = __ldg(B + B_P0 * L + r + 2);
-        w.T0 = __ldg(B + B_T0 * L + r + 2);
+        const Real* B = static_cast<const Real*>(a.base) + base_index(0, r);
+        w.rho0 = __ldg(B + B_RHO0);
+        w.p0 = __ldg(B + B_P0);
+        w.T0 = __ldg(B + B_T0);
     } else {
         w.rho0 = Real(0); w.p0 = Real(0); w.T0 = Real(0);
     }
@@ -485,8 +484,7 @@ __device__ __forceinline__ void step_block(const StepArgs& a, const int tile, co
     const Real mu = kc.mu, kappa = kc.kappa, eta = kc.eta;
     const Real invdx[3] = {kc.invdx[0], kc.invdx[1], kc.invdx[2]};
     const Real* __restrict__ Bt = static_cast<const Real*>(a.base);
-    const int BL = nv + 4;
-    auto base = [&](int field, int r) -> Real { return SPLIT ? __ldg(Bt + field * BL + r + 2) : Real(0); };
+    auto base = [&](int field, int r) -> Real { return SPLIT ? __ldg(Bt + base_index(field, r)) : Real(0); };
 
     // this thread's output cell
     const int olx = tid % TX, oly = tid / TX;

@@ -5,21 +5,26 @@
 // organised for a kernel whose cost is instruction issue rather than FP64
 // throughput: every thread owns one column (lx, ly) of the tile plus its
 // two-cell in-plane halo, R2X x R2Y threads in all, and keeps that column's
-// whole vertical pipeline in registers -- primitives of planes f and f-1,
-// the faces between them, tilde states of planes f-1 and f-2, the upwind
-// flux through the lower face, the dissipative carries.  Shared memory only
-// exchanges in-plane neighbours, at constant offsets (t +- 1, t +- R2X), so
-// no index arithmetic is left in the plane loop.  One warp spans a row of 32
-// columns (3D: 28 output cells plus the halo).
+// whole vertical pipeline in registers -- conserved and face values of the
+// planes behind the front, tilde states, the upwind flux through the lower
+// face, the viscous z flux.  Shared memory only exchanges in-plane
+// neighbours: every exchange array is single-buffered at a fixed offset, so
+// each access is the thread's own slot plus a constant.
 //
-// Per front plane f (one __syncthreads after each of A-D):
-//   A  own cell of plane f: primitives (registers), in-plane exchange copies;
-//   B  own +x / +y faces of plane f, own z face (f-1, f);
-//   C  tilde state of plane f-1 (own), dissipative fluxes of plane f-1's
-//      own +x / +y faces and of the z face (f-1, f);
-//   D  upwind transport fluxes of plane f-2's own +x / +y faces, the z face
-//      (f-2, f-1), the in-plane viscous divergence of plane f-1;
-//   E  update of plane f-2 (own cell), store, CFL wave rate.
+// The vertical pipeline is skewed so that one plane needs two barriers.  At
+// front plane f:
+//   H1  own cell of plane f (primitives; exchange X), z face (f-1, f),
+//       tilde state of plane f-1, viscous fluxes of plane f-2's own +x / +y
+//       faces (exchange VF) and of the z face (f-2, f-1), upwind transport
+//       fluxes of plane f-2's own +x / +y faces (exchange TF) and z face;
+//   --- barrier
+//   H2  own +x / +y acoustic faces of plane f from X (exchange FF, read in
+//       the next H1); exchange of the tilde state of plane f-1 (TL) and of the
+//       velocity / temperature data the next plane's viscous fluxes need (VT,
+//       DZ, SZ); update of plane f-2 from TF and VF, store, CFL wave rate;
+//   --- barrier
+// Each exchange array is written in one half and read in the other, so one
+// buffer of each suffices.
 #pragma once
 
 #include "ark_step.cuh"
@@ -37,28 +42,39 @@ struct Step2Cfg {
     static constexpr int NV = DIM + 1;                            // dissipative flux components
     static constexpr int NDIR = DIM - 1;                          // in-plane directions
     // shared memory, in units of Real, each array indexed by thread
-    static constexpr int O_PX = 0;                                // [2][NPX][NT]
-    static constexpr int O_VT = O_PX + 2 * NPX * NT;              // [3][NVT][NT]
-    static constexpr int O_F = O_VT + (VISC ? 3 * NVT * NT : 0);   // [2][NDIR][2][NT]  (u*, dPi*)
-    static constexpr int O_TL = O_F + 2 * NDIR * 2 * NT;          // [2][NF][NT]
-    static constexpr int O_VF = O_TL + 2 * NF * NT;               // [NDIR][NV][NT]
-    static constexpr int O_TF = O_VF + (VISC ? NDIR * NV * NT : 0);   // [NDIR][NF][NT]
-    static constexpr int N_REAL = O_TF + NDIR * NF * NT;
+    static constexpr int O_X = 0;                                 // [NPX]       plane f primitives
+    static constexpr int O_FF = O_X + NPX * NT;                   // [NDIR][2]   u*, dPi* of own in-plane faces
+    static constexpr int O_TL = O_FF + NDIR * 2 * NT;             // [NF]        tilde state
+    static constexpr int O_TF = O_TL + NF * NT;                   // [NDIR][NF]  upwind transport fluxes
+    static constexpr int O_VT = O_TF + NDIR * NF * NT;            // [NVT]       velocity, T (VISC)
+    static constexpr int O_DZ = O_VT + (VISC ? NVT * NT : 0);     // [D]         vertical velocity difference (VISC)
+    static constexpr int O_SZ = O_DZ + (VISC ? D * NT : 0);       // [D]         velocity sum of two planes (VISC)
+    static constexpr int O_VF = O_SZ + (VISC ? D * NT : 0);       // [NDIR][NV]  dissipative fluxes (VISC)
+    static constexpr int N_REAL = O_VF + (VISC ? NDIR * NV * NT : 0);
     static constexpr size_t SMEM_BYTES = ((N_REAL * sizeof(Real) + 15) / 16) * 16 + NT * sizeof(double) + 4 * sizeof(double);
     static_assert(NT % 32 == 0 && NT <= 1024, "block must be whole warps");
 };
+
+// Four consecutive base-table entries of one row (16-byte aligned).
+struct Base4 {
+    float x, y, z, w;
+};
+__device__ __forceinline__ Base4 base4(const float* __restrict__ Bt, int group, int r)
+{
+    const float4 v = __ldg(reinterpret_cast<const float4*>(Bt + base_index(4 * group, r)));
+    return Base4{v.x, v.y, v.z, v.w};
+}
 
 template <int DIM, typename Real, bool SPLIT, bool VISC, int R2X, int R2Y>
 __device__ __forceinline__ void step_block2(const StepArgs& a, const int tile, const int chunk, unsigned char* smem_raw)
 {
     using C = Step2Cfg<DIM, Real, SPLIT, VISC, R2X, R2Y>;
-    using C1 = StepCfg<DIM, Real, SPLIT, VISC, C::TX, C::TY>;   // for the loader's Stepper type
     constexpr int D = DIM, NF = DIM + 2, V = DIM - 1, NT = C::NT, TX = C::TX, TY = C::TY;
+    static_assert(!SPLIT || sizeof(Real) == 4, "the split form stores FP32 deviations");
     Real* sm = reinterpret_cast<Real*>(smem_raw);
     double* red = reinterpret_cast<double*>(smem_raw + ((C::N_REAL * sizeof(Real) + 15) / 16) * 16);
 
     const Stepper<DIM, Real, SPLIT, VISC, C::TX, C::TY> S(a);
-    (void)sizeof(C1);
     const int t = threadIdx.x;
     const int lx = t % R2X - 2, ly = t / R2X - C::HY;
     const int x0 = (tile % a.tiles_x) * TX;
@@ -98,74 +114,100 @@ __device__ __forceinline__ void step_block2(const StepArgs& a, const int tile, c
     Real lam[3];
 #pragma unroll
     for (int d = 0; d < 3; ++d) lam[d] = sdt[1 + d];
-    const Real* __restrict__ Bt = static_cast<const Real*>(a.base);
-    const int BL = nv + 4;
-    auto base = [&](int field, int r) -> Real { return SPLIT ? __ldg(Bt + field * BL + r + 2) : Real(0); };
+    const float* __restrict__ Bt = static_cast<const float*>(a.base);
 
-    // loader position of this column (clamped into the ghost range)
+    // loader position of this column (clamped into the ghost range); cell
+    // offsets within a field are 32-bit (the FP32 forms need ncell < 2^32)
     const int gx = min(max(x0 + lx, -2), nx + 1);
     const int gy = D == 3 ? min(max(y0 + ly, -2), ny + 1) : 0;
     const bool colin = gx >= 0 && gx < nx && (D == 2 || (gy >= 0 && gy < ny));
-    const long long cidx = D == 3 ? gx + (long long)nx * gy : gx;
-    const long long plane_cells = D == 3 ? (long long)nx * ny : (long long)nx;
+    const unsigned plane_cells = D == 3 ? (unsigned)nx * (unsigned)ny : (unsigned)nx;
+    const unsigned cidx = D == 3 ? (unsigned)gx + (unsigned)nx * (unsigned)gy : (unsigned)gx;
     const bool ocol = inT && (x0 + lx) < nx && (D == 2 || (y0 + ly) < ny);
-    const long long oidx = D == 3 ? (x0 + lx) + (long long)nx * (y0 + ly) : (x0 + lx);
+    const unsigned oidx = D == 3 ? (unsigned)(x0 + lx) + (unsigned)nx * (unsigned)(y0 + ly) : (unsigned)(x0 + lx);
+    const Real* __restrict__ Uin = S.U;
+    Real* __restrict__ Uo = static_cast<Real*>(a.Uout);
 
     Real raw[NF];
     auto prefetch = [&](int p) {
         if (colin && p >= 0 && p < nv) {
-            const long long idx = cidx + plane_cells * p;
+            const unsigned idx = cidx + plane_cells * (unsigned)p;
 #pragma unroll
-            for (int k = 0; k < NF; ++k) raw[k] = __ldg(S.U + k * N + idx);
+            for (int k = 0; k < NF; ++k) raw[k] = __ldg(Uin + k * N + idx);
         }
     };
     prefetch(z0 - 2);
+
+    // exchange arrays: this thread's slot of each
+    Real* const X = sm + C::O_X + t;
+    Real* const FF = sm + C::O_FF + t;
+    Real* const TL = sm + C::O_TL + t;
+    Real* const TF = sm + C::O_TF + t;
+    Real* const VT = sm + C::O_VT + t;
+    Real* const DZ = sm + C::O_DZ + t;
+    Real* const SZ = sm + C::O_SZ + t;
+    Real* const VF = sm + C::O_VF + t;
+    constexpr int SX = 1, SY = R2X;
 
     // own-column registers
     struct Prev {                     // plane f-1: conserved values and face inputs
         Real drho, m[D], dW, dp, z, rz, rc;
     } cp;
+    cp.drho = cp.dW = cp.dp = cp.z = cp.rz = cp.rc = 0;
+#pragma unroll
+    for (int d = 0; d < D; ++d) cp.m[d] = 0;
     Real fxp[2] = {0, 0}, fyp[2] = {0, 0};   // own +x / +y faces of plane f-1 (u*, dPi*)
     Real fx2 = 0, fy2 = 0;            // u* of the own +x / +y faces of plane f-2
     Real zfl[3] = {0, 0, 0};          // face (f-2, f-1): u*, dPi*, dS
     Real tlA[NF + 1];                 // tilde state (+ L) of plane f-2
     Real vt2[C::NVT], vt1[C::NVT];    // velocity (+T) of planes f-2, f-1
-    Real zt_lo[NF];
+    Real zt_lo[NF];                   // upwind transport flux through the face (f-3, f-2)
     Real us_lo = 0;
-    Real zvA[C::NV], zvB[C::NV], dxy_prev[C::NV];
+    Real zvA[C::NV];                  // dissipative flux through the face (f-3, f-2)
 #pragma unroll
     for (int k = 0; k <= NF; ++k) tlA[k] = 0;
 #pragma unroll
     for (int k = 0; k < NF; ++k) zt_lo[k] = 0;
 #pragma unroll
-    for (int k = 0; k < C::NV; ++k) zvA[k] = zvB[k] = dxy_prev[k] = 0;
+    for (int k = 0; k < C::NV; ++k) zvA[k] = 0;
 #pragma unroll
     for (int k = 0; k < C::NVT; ++k) vt2[k] = vt1[k] = 0;
     Real smax_t = 0;
     unsigned status = 0u;
 
-    constexpr int SX = 1, SY = R2X;
-
     for (int f = z0 - 2; f <= z1 + 1; ++f) {
         const Real fr = Real(f);
-        const int s3 = ((f % 3) + 3) % 3;
-        Real* const PXf = sm + C::O_PX + (f & 1) * C::NPX * NT;
-        Real* const VT0 = sm + C::O_VT + s3 * C::NVT * NT;                    // plane f
-        Real* const VT1 = sm + C::O_VT + ((s3 + 2) % 3) * C::NVT * NT;        // plane f-1
-        Real* const VT2 = sm + C::O_VT + ((s3 + 1) % 3) * C::NVT * NT;        // plane f-2
-        Real* const Ff = sm + C::O_F + (f & 1) * C::NDIR * 2 * NT;            // in-plane faces of plane f
-        Real* const Ff1 = sm + C::O_F + ((f - 1) & 1) * C::NDIR * 2 * NT;     // of plane f-1
-        Real* const TL1 = sm + C::O_TL + ((f - 1) & 1) * NF * NT;             // tilde of plane f-1
-        Real* const TL2 = sm + C::O_TL + ((f - 2) & 1) * NF * NT;             // tilde of plane f-2
-        Real* const VF = sm + C::O_VF;
-        Real* const TF = sm + C::O_TF;
+        // base rows of the planes this pass touches (split form)
+        Base4 bf0{}, b10{}, b11{}, b20{}, b22{}, b23{}, b32{};
+        if constexpr (SPLIT) {
+            bf0 = base4(Bt, 0, f);        // row f:   rho0, p0, T0, H0
+            if (f >= z0) {
+                b10 = base4(Bt, 0, f - 1);  // row f-1: rho0, p0, T0, H0
+                b11 = base4(Bt, 1, f - 1);  //          R0F, Q0, DPP, DPM
+            } else if (f >= z0 - 1) {
+                b11 = base4(Bt, 1, f - 1);
+            }
+            if (f >= z0 + 1) {
+                b22 = base4(Bt, 2, f - 2);  // row f-2: DRP, DRM, DWP, DWM
+                if (f >= z0 + 2) {
+                    b20 = base4(Bt, 0, f - 2);
+                    b23 = base4(Bt, 3, f - 2);  //      DQ0
+                    b32 = base4(Bt, 2, f - 3);  // row f-3: DRP, DRM, DWP, DWM
+                }
+            }
+        }
 
-        // ---------------- A: own cell of plane f ----------------
+        // ================= H1 =================
+        // own cell of plane f
         Cell<D, Real> cc;
         {
             const bool fin = f >= 0 && f < nv;
             if (fin && colin) {
-                const Row<Real> w = row_info<Real, SPLIT>(a, S.phi, f, nv, fr);
+                Row<Real> w;
+                w.rho0 = SPLIT ? bf0.x : Real(0);
+                w.p0 = SPLIT ? bf0.y : Real(0);
+                w.T0 = SPLIT ? bf0.z : Real(0);
+                w.phi = a.energy_form ? Real(0) : S.phi.at(fr);
                 cc.drho = raw[0];
 #pragma unroll
                 for (int d = 0; d < D; ++d) cc.m[d] = raw[1 + d];
@@ -178,120 +220,91 @@ __device__ __forceinline__ void step_block2(const StepArgs& a, const int tile, c
         prefetch(f + 1);
         const Real rcc = cc.rc;
         const Real zc = cc.rho * cc.c, rzc = rcc * cc.rr;
-        PXf[0 * NT + t] = cc.u[0];
-        if constexpr (D == 3) PXf[1 * NT + t] = cc.u[1];
-        PXf[(C::NPX - 4) * NT + t] = cc.dp;
-        PXf[(C::NPX - 3) * NT + t] = zc;
-        PXf[(C::NPX - 2) * NT + t] = rzc;
-        PXf[(C::NPX - 1) * NT + t] = rcc;
+        X[0 * NT] = cc.u[0];
+        if constexpr (D == 3) X[1 * NT] = cc.u[1];
+        X[(C::NPX - 4) * NT] = cc.dp;
+        X[(C::NPX - 3) * NT] = zc;
+        X[(C::NPX - 2) * NT] = rzc;
+        X[(C::NPX - 1) * NT] = rcc;
         Real vt0[C::NVT];
 #pragma unroll
         for (int d = 0; d < D; ++d) vt0[d] = cc.u[d];
         if constexpr (VISC) vt0[D] = cc.dT;
-        if constexpr (VISC) {
-#pragma unroll
-            for (int k = 0; k < C::NVT; ++k) VT0[k * NT + t] = vt0[k];
-        }
-        __syncthreads();
 
-        // ---------------- B: own +x / +y faces of plane f, own z face (f-1, f) ----------------
-        Real fxc[2] = {0, 0}, fyc[2] = {0, 0};
-        if (f >= z0 - 1) {
-            if (xfR1) {
-                const int j = t + SX;
-                acoustic_face<Real>(cc.u[0], PXf[j], cc.dp, PXf[(C::NPX - 4) * NT + j], zc, PXf[(C::NPX - 3) * NT + j],
-                                    rzc, PXf[(C::NPX - 2) * NT + j], rcc, PXf[(C::NPX - 1) * NT + j], Real(0), Real(0),
-                                    kc.K, kc.halfInvK, a.low_mach, fxc[0], fxc[1]);
-                Ff[0 * NT + t] = fxc[0];
-                Ff[1 * NT + t] = fxc[1];
-            }
-            if constexpr (D == 3) {
-                if (yfR1) {
-                    const int j = t + SY;
-                    acoustic_face<Real>(cc.u[1], PXf[NT + j], cc.dp, PXf[2 * NT + j], zc, PXf[3 * NT + j], rzc,
-                                        PXf[4 * NT + j], rcc, PXf[5 * NT + j], Real(0), Real(0), kc.K, kc.halfInvK,
-                                        a.low_mach, fyc[0], fyc[1]);
-                    Ff[2 * NT + t] = fyc[0];
-                    Ff[3 * NT + t] = fyc[1];
-                }
-            }
-        }
-        Real zfu[3] = {0, 0, 0};   // face (f-1, f)
+        // own z face (f-1, f)
+        Real zfu[3] = {0, 0, 0};
         if (f >= z0 - 1 && inR1) {
             const Real dphi = S.phi.at(fr) - S.phi.at(fr - Real(1));
             zfu[2] = Real(-0.5) * (cp.drho + cc.drho) * dphi;
-            acoustic_face<Real>(vt1[V], cc.u[V], cp.dp, cc.dp, cp.z, zc, cp.rz, rzc, cp.rc, rcc, base(B_R0F, f - 1),
-                                zfu[2], kc.K, kc.halfInvK, a.low_mach, zfu[0], zfu[1]);
+            acoustic_face<Real>(vt1[V], cc.u[V], cp.dp, cc.dp, cp.z, zc, cp.rz, rzc, cp.rc, rcc,
+                                SPLIT ? Real(b11.x) : Real(0), zfu[2], kc.K, kc.halfInvK, a.low_mach, zfu[0], zfu[1]);
         }
-        __syncthreads();
 
-        // ---------------- C: tilde of plane f-1; dissipative fluxes of plane f-1 ----------------
+        // tilde state of plane f-1
         Real tlB[NF + 1];
 #pragma unroll
         for (int k = 0; k <= NF; ++k) tlB[k] = 0;
         if (f >= z0 && inR1) {
             const int q1 = f - 1;
-            const Real usx_m = Ff1[t - SX], pix_m = Ff1[NT + t - SX];
+            const Real usx_m = FF[0 * NT - SX], pix_m = FF[1 * NT - SX];
             Real ell = lam[0] * (fxp[0] - usx_m);
             Real m_t[D];
             m_t[0] = cp.m[0] - lam[0] * (fxp[1] - pix_m);
             Real W_t = cp.dW - lam[0] * (fxp[1] * fxp[0] - pix_m * usx_m);
             if constexpr (D == 3) {
-                const Real usy_m = Ff1[2 * NT + t - SY], piy_m = Ff1[3 * NT + t - SY];
+                const Real usy_m = FF[2 * NT - SY], piy_m = FF[3 * NT - SY];
                 ell += lam[1] * (fyp[0] - usy_m);
                 m_t[1] = cp.m[1] - lam[1] * (fyp[1] - piy_m);
                 W_t -= lam[1] * (fyp[1] * fyp[0] - piy_m * usy_m);
             }
             ell += lam[V] * (zfu[0] - zfl[0]);
             m_t[V] = cp.m[V] - lam[V] * (zfu[1] - zfl[1]) + lam[V] * Real(0.5) * (zfu[2] + zfl[2]);
-            if constexpr (SPLIT) m_t[V] -= lam[V] * base(B_Q0, q1);
+            if constexpr (SPLIT) m_t[V] -= lam[V] * Real(b11.y);
             W_t -= lam[V] * (zfu[1] * zfu[0] - zfl[1] * zfl[0]);
-            if constexpr (SPLIT) W_t -= lam[V] * (base(B_DPP, q1) * zfu[0] - base(B_DPM, q1) * zfl[0]) + base(B_H0, q1) * ell;
+            if constexpr (SPLIT) W_t -= lam[V] * (Real(b11.z) * zfu[0] - Real(b11.w) * zfl[0]) + Real(b10.w) * ell;
             if (a.energy_form) W_t += lam[V] * Real(0.5) * (zfu[0] * zfu[2] + zfl[0] * zfl[2]);   // (uS)_i, Appendix B
             const Real L = Real(1) + ell;
             const Real rL = rcp(L);
-            tlB[0] = SPLIT ? (cp.drho - base(B_RHO0, q1) * ell) * rL : cp.drho * rL;
+            tlB[0] = SPLIT ? (cp.drho - Real(b10.x) * ell) * rL : cp.drho * rL;
 #pragma unroll
             for (int d = 0; d < D; ++d) tlB[1 + d] = m_t[d] * rL;
             tlB[D + 1] = W_t * rL;
             tlB[NF] = L;
-#pragma unroll
-            for (int k = 0; k < NF; ++k) TL1[k * NT + t] = tlB[k];
             const bool valid = (x0 + lx) >= 0 && (x0 + lx) < nx && (D == 2 || ((y0 + ly) >= 0 && (y0 + ly) < ny)) &&
                                q1 >= 0 && q1 < nv;
             if (valid && !(L > Real(0))) status |= ST_LTILDE;
         }
+
+        // dissipative fluxes of plane f-2's own +x / +y faces and of the z face (f-2, f-1)
         Real zv_new[C::NV];
 #pragma unroll
         for (int k = 0; k < C::NV; ++k) zv_new[k] = 0;
         if constexpr (VISC) {
             const Real mu = kc.mu, kappa = kc.kappa, eta = kc.eta;
-            // own +x (and +y) faces of plane f-1's output cells
-            if (f >= z0 + 1 && f <= z1) {
+            if (f >= z0 + 2) {
                 auto face = [&](auto dirc) {
                     constexpr int dir = decltype(dirc)::value;
                     constexpr int sh = dir == 0 ? SX : SY;
-                    const int j = t + sh;
                     Real grad[3][3];
 #pragma unroll
                     for (int aa = 0; aa < 3; ++aa)
 #pragma unroll
                         for (int qq = 0; qq < 3; ++qq) grad[aa][qq] = 0;
 #pragma unroll
-                    for (int qq = 0; qq < D; ++qq) grad[dir][qq] = (VT1[qq * NT + j] - vt1[qq]) * kc.invdx[dir];
+                    for (int qq = 0; qq < D; ++qq) grad[dir][qq] = (VT[qq * NT + sh] - vt2[qq]) * kc.invdx[dir];
                     if constexpr (D == 3) {
                         constexpr int tt = 1 - dir;
                         constexpr int st = tt == 0 ? SX : SY;
 #pragma unroll
                         for (int qq = 0; qq < D; ++qq)
                             grad[tt][qq] = Real(0.25) *
-                                           ((VT1[qq * NT + t + st] - VT1[qq * NT + t - st]) +
-                                            (VT1[qq * NT + j + st] - VT1[qq * NT + j - st])) *
+                                           ((VT[qq * NT + st] - VT[qq * NT - st]) +
+                                            (VT[qq * NT + sh + st] - VT[qq * NT + sh - st])) *
                                            kc.invdx[tt];
                     }
 #pragma unroll
                     for (int qq = 0; qq < D; ++qq)
-                        grad[V][qq] = Real(0.25) * ((vt0[qq] - vt2[qq]) + (VT0[qq * NT + j] - VT2[qq * NT + j])) * kc.invdx[V];
+                        grad[V][qq] = Real(0.25) * (DZ[qq * NT] + DZ[qq * NT + sh]) * kc.invdx[V];
                     Real divu = 0;
 #pragma unroll
                     for (int aa = 0; aa < D; ++aa) divu += grad[aa][aa];
@@ -300,34 +313,30 @@ __device__ __forceinline__ void step_block2(const StepArgs& a, const int tile, c
                     for (int qq = 0; qq < D; ++qq) {
                         Real tau = mu * (grad[dir][qq] + grad[qq][dir]);
                         if (qq == dir) tau += eta * divu;
-                        work += tau * Real(0.5) * (vt1[qq] + VT1[qq * NT + j]);
-                        VF[(dir * C::NV + qq) * NT + t] = tau;
+                        work += tau * Real(0.5) * (vt2[qq] + VT[qq * NT + sh]);
+                        VF[(dir * C::NV + qq) * NT] = tau;
                     }
-                    VF[(dir * C::NV + D) * NT + t] = work + kappa * (VT1[D * NT + j] - vt1[D]) * kc.invdx[dir];
+                    VF[(dir * C::NV + D) * NT] = work + kappa * (VT[D * NT + sh] - vt2[D]) * kc.invdx[dir];
                 };
                 if (xfT) face(IC<0>{});
                 if constexpr (D == 3) {
                     if (yfT) face(IC<1>{});
                 }
             }
-            // own z face (f-1, f)
-            if (f >= z0 && f <= z1 && inT) {
+            if (f >= z0 + 1 && inT) {
                 Real grad[3][3];
 #pragma unroll
                 for (int aa = 0; aa < 3; ++aa)
 #pragma unroll
                     for (int qq = 0; qq < 3; ++qq) grad[aa][qq] = 0;
 #pragma unroll
-                for (int qq = 0; qq < D; ++qq) grad[V][qq] = (vt0[qq] - vt1[qq]) * kc.invdx[V];
+                for (int qq = 0; qq < D; ++qq) grad[V][qq] = (vt1[qq] - vt2[qq]) * kc.invdx[V];
 #pragma unroll
                 for (int tt = 0; tt < D - 1; ++tt) {
                     const int st = tt == 0 ? SX : SY;
 #pragma unroll
                     for (int qq = 0; qq < D; ++qq)
-                        grad[tt][qq] = Real(0.25) *
-                                       ((VT1[qq * NT + t + st] - VT1[qq * NT + t - st]) +
-                                        (VT0[qq * NT + t + st] - VT0[qq * NT + t - st])) *
-                                       kc.invdx[tt];
+                        grad[tt][qq] = Real(0.25) * (SZ[qq * NT + st] - SZ[qq * NT - st]) * kc.invdx[tt];
                 }
                 Real divu = 0;
 #pragma unroll
@@ -337,37 +346,24 @@ __device__ __forceinline__ void step_block2(const StepArgs& a, const int tile, c
                 for (int qq = 0; qq < D; ++qq) {
                     Real tau = mu * (grad[V][qq] + grad[qq][V]);
                     if (qq == V) tau += eta * divu;
-                    work += tau * Real(0.5) * (vt1[qq] + vt0[qq]);
+                    work += tau * Real(0.5) * (vt2[qq] + vt1[qq]);
                     zv_new[qq] = tau;
                 }
-                zv_new[D] = work + kappa * (vt0[D] - vt1[D]) * kc.invdx[V];
+                zv_new[D] = work + kappa * (vt1[D] - vt2[D]) * kc.invdx[V];
             }
         }
-        __syncthreads();
 
-        // ---------------- D: transport fluxes of plane f-2, viscous divergence of plane f-1 ----------------
-        Real dxy_new[C::NV];
-#pragma unroll
-        for (int k = 0; k < C::NV; ++k) dxy_new[k] = 0;
-        if constexpr (VISC) {
-            if (f >= z0 + 1 && f <= z1 && inT) {
-#pragma unroll
-                for (int k = 0; k < C::NV; ++k) dxy_new[k] = (VF[k * NT + t] - VF[k * NT + t - SX]) * lam[0];
-                if constexpr (D == 3) {
-#pragma unroll
-                    for (int k = 0; k < C::NV; ++k)
-                        dxy_new[k] += (VF[(C::NV + k) * NT + t] - VF[(C::NV + k) * NT + t - SY]) * lam[1];
-                }
-            }
-        }
+        // upwind transport fluxes of plane f-2's own +x / +y faces
         Real tfx[NF], tfy[NF];
+#pragma unroll
+        for (int k = 0; k < NF; ++k) tfx[k] = tfy[k] = 0;
         if (f >= z0 + 2) {
             if (xfT) {
                 const bool upL = fx2 >= Real(0);
 #pragma unroll
                 for (int k = 0; k < NF; ++k) {
-                    tfx[k] = (upL ? tlA[k] : TL2[k * NT + t + SX]) * fx2;
-                    TF[k * NT + t] = tfx[k];
+                    tfx[k] = (upL ? tlA[k] : TL[k * NT + SX]) * fx2;
+                    TF[k * NT] = tfx[k];
                 }
             }
             if constexpr (D == 3) {
@@ -375,14 +371,15 @@ __device__ __forceinline__ void step_block2(const StepArgs& a, const int tile, c
                     const bool upL = fy2 >= Real(0);
 #pragma unroll
                     for (int k = 0; k < NF; ++k) {
-                        tfy[k] = (upL ? tlA[k] : TL2[k * NT + t + SY]) * fy2;
-                        TF[(NF + k) * NT + t] = tfy[k];
+                        tfy[k] = (upL ? tlA[k] : TL[k * NT + SY]) * fy2;
+                        TF[(NF + k) * NT] = tfy[k];
                     }
                 }
             }
         }
+        // ... and of the z face (f-2, f-1)
         Real zt_hi[NF];
-        Real us_hi = zfl[0];   // u* of the face (f-2, f-1)
+        const Real us_hi = zfl[0];
 #pragma unroll
         for (int k = 0; k < NF; ++k) zt_hi[k] = 0;
         if (f >= z0 + 1 && inT) {
@@ -391,14 +388,50 @@ __device__ __forceinline__ void step_block2(const StepArgs& a, const int tile, c
             for (int k = 0; k < NF; ++k) zt_hi[k] = (upL ? tlA[k] : tlB[k]) * us_hi;
             if constexpr (SPLIT) {
                 if (!upL) {
-                    zt_hi[0] += base(B_DRP, f - 2) * us_hi;
-                    zt_hi[D + 1] += base(B_DWP, f - 2) * us_hi;
+                    zt_hi[0] += Real(b22.x) * us_hi;
+                    zt_hi[D + 1] += Real(b22.z) * us_hi;
                 }
             }
         }
         __syncthreads();
 
-        // ---------------- E: update of plane f-2 ----------------
+        // ================= H2 =================
+        // own +x / +y acoustic faces of plane f
+        Real fxc[2] = {0, 0}, fyc[2] = {0, 0};
+        if (f >= z0 - 1 && f <= z1) {
+            if (xfR1) {
+                acoustic_face<Real>(cc.u[0], X[SX], cc.dp, X[(C::NPX - 4) * NT + SX], zc, X[(C::NPX - 3) * NT + SX],
+                                    rzc, X[(C::NPX - 2) * NT + SX], rcc, X[(C::NPX - 1) * NT + SX], Real(0), Real(0),
+                                    kc.K, kc.halfInvK, a.low_mach, fxc[0], fxc[1]);
+                FF[0 * NT] = fxc[0];
+                FF[1 * NT] = fxc[1];
+            }
+            if constexpr (D == 3) {
+                if (yfR1) {
+                    acoustic_face<Real>(cc.u[1], X[NT + SY], cc.dp, X[2 * NT + SY], zc, X[3 * NT + SY], rzc,
+                                        X[4 * NT + SY], rcc, X[5 * NT + SY], Real(0), Real(0), kc.K, kc.halfInvK,
+                                        a.low_mach, fyc[0], fyc[1]);
+                    FF[2 * NT] = fyc[0];
+                    FF[3 * NT] = fyc[1];
+                }
+            }
+        }
+        // exchange for the next plane's H1
+        if (inR1) {
+#pragma unroll
+            for (int k = 0; k < NF; ++k) TL[k * NT] = tlB[k];
+            if constexpr (VISC) {
+#pragma unroll
+                for (int k = 0; k < C::NVT; ++k) VT[k * NT] = vt1[k];
+#pragma unroll
+                for (int d = 0; d < D; ++d) {
+                    DZ[d * NT] = vt0[d] - vt2[d];
+                    SZ[d * NT] = vt1[d] + vt0[d];
+                }
+            }
+        }
+
+        // update of plane f-2
         if (f >= z0 + 2 && inT) {
             const int q = f - 2;
             const Real L = tlA[NF];
@@ -406,8 +439,8 @@ __device__ __forceinline__ void step_block2(const StepArgs& a, const int tile, c
 #pragma unroll
             for (int k = 0; k < NF; ++k) {
                 Real acc = tlA[k] * L;
-                acc -= lam[0] * (tfx[k] - TF[k * NT + t - SX]);
-                if constexpr (D == 3) acc -= lam[1] * (tfy[k] - TF[(NF + k) * NT + t - SY]);
+                acc -= lam[0] * (tfx[k] - TF[k * NT - SX]);
+                if constexpr (D == 3) acc -= lam[1] * (tfy[k] - TF[(NF + k) * NT - SY]);
                 nb[k] = acc;
             }
             Real lowfix[NF];
@@ -415,26 +448,33 @@ __device__ __forceinline__ void step_block2(const StepArgs& a, const int tile, c
             for (int k = 0; k < NF; ++k) lowfix[k] = zt_lo[k];
             if constexpr (SPLIT) {
                 if (us_lo >= Real(0)) {
-                    lowfix[0] += base(B_DRM, q) * us_lo;
-                    lowfix[D + 1] += base(B_DWM, q) * us_lo;
+                    lowfix[0] += Real(b22.y) * us_lo;
+                    lowfix[D + 1] += Real(b22.w) * us_lo;
                 } else {
-                    lowfix[0] -= base(B_DRP, q - 1) * us_lo;
-                    lowfix[D + 1] -= base(B_DWP, q - 1) * us_lo;
+                    lowfix[0] -= Real(b32.x) * us_lo;
+                    lowfix[D + 1] -= Real(b32.z) * us_lo;
                 }
             }
 #pragma unroll
             for (int k = 0; k < NF; ++k) nb[k] -= lam[V] * (zt_hi[k] - lowfix[k]);
             if constexpr (VISC) {
 #pragma unroll
-                for (int k = 0; k < C::NV; ++k) nb[1 + k] += dxy_prev[k] + (zvB[k] - zvA[k]) * lam[V];
-                if constexpr (SPLIT) nb[D + 1] += dt * base(B_DQ0, q);
+                for (int k = 0; k < C::NV; ++k) {
+                    Real dxy = (VF[k * NT] - VF[k * NT - SX]) * lam[0];
+                    if constexpr (D == 3) dxy += (VF[(C::NV + k) * NT] - VF[(C::NV + k) * NT - SY]) * lam[1];
+                    nb[1 + k] += dxy + (zv_new[k] - zvA[k]) * lam[V];
+                }
+                if constexpr (SPLIT) nb[D + 1] += dt * Real(b23.x);
             }
             if (ocol) {
-                Real* Uo = static_cast<Real*>(a.Uout);
-                const long long idx = oidx + plane_cells * q;
+                const unsigned idx = oidx + plane_cells * (unsigned)q;
 #pragma unroll
                 for (int k = 0; k < NF; ++k) Uo[k * N + idx] = nb[k];
-                const Row<Real> w = row_info<Real, SPLIT>(a, S.phi, q, nv, fr - Real(2));
+                Row<Real> w;
+                w.rho0 = SPLIT ? Real(b20.x) : Real(0);
+                w.p0 = SPLIT ? Real(b20.y) : Real(0);
+                w.T0 = SPLIT ? Real(b20.z) : Real(0);
+                w.phi = a.energy_form ? Real(0) : S.phi.at(fr - Real(2));
                 Real p, rho;
                 const Real sh = wave_rate<D, Real, SPLIT, VISC>(nb, w, S.gm1, S.gamma, kc.invdx, kc.mu, kc.kappa, p, rho);
                 if (!(sh <= smax_t)) smax_t = (sh == sh) ? sh : smax_t;
@@ -442,6 +482,7 @@ __device__ __forceinline__ void step_block2(const StepArgs& a, const int tile, c
                 if (!(rho > Real(0)) || !(p > Real(0))) status |= ST_NONPHYS;
             }
         }
+        __syncthreads();
 
         // ---------------- rotate the column registers ----------------
         if (f >= z0 + 1) {
@@ -450,11 +491,7 @@ __device__ __forceinline__ void step_block2(const StepArgs& a, const int tile, c
             us_lo = us_hi;
         }
 #pragma unroll
-        for (int k = 0; k < C::NV; ++k) {
-            zvA[k] = zvB[k];
-            zvB[k] = zv_new[k];
-            dxy_prev[k] = dxy_new[k];
-        }
+        for (int k = 0; k < C::NV; ++k) zvA[k] = zv_new[k];
 #pragma unroll
         for (int k = 0; k <= NF; ++k) tlA[k] = tlB[k];
         fx2 = fxp[0];
