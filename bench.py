@@ -71,20 +71,25 @@ def measured_peaks():
 
 
 def kernel_traffic(path):
-    """DRAM bytes per launch of the step kernel from a committed ncu summary,
-    valid only while the kernel source is unchanged (hash recorded with it)."""
+    """DRAM bytes per launch of the step kernel from the committed ncu figures
+    (profiles/step_kernel_traffic.txt), valid only while the step kernel
+    sources are unchanged (their hash is recorded with the figures)."""
     import hashlib
     try:
-        with open(os.path.join(ROOT, "profiles", "step_kernel_traffic.json")) as f:
-            rec = json.load(f)
+        rec = {}
+        with open(os.path.join(ROOT, "profiles", "step_kernel_traffic.txt")) as f:
+            for line in f:
+                parts = line.split()
+                if len(parts) == 2 and not line.startswith("#"):
+                    rec[parts[0]] = parts[1]
         h = hashlib.sha256()
-        for name in ("ark_step.cuh", "ark_common.cuh"):
+        for name in ("ark_common.cuh", "ark_step.cuh", "ark_step2.cuh"):
             with open(os.path.join(ROOT, "paper_1903_09043_gb300", "csrc", name), "rb") as g:
                 h.update(g.read())
         if rec.get("source_sha256") != h.hexdigest():
             return None
-        ent = rec.get("paths", {}).get(path)
-        return ent.get("bytes_per_launch_full") if ent else None
+        v = rec.get(f"{path}.bytes_per_launch_full")
+        return float(v) if v is not None else None
     except Exception:
         return None
 
