@@ -154,13 +154,22 @@ def dist_setup():
 
 
 def barrier_and_max(value, world):
+    """Maximum of a per-rank value over all ranks (the slowest rank's time)."""
     if world <= 1:
         return value
     import torch
     import torch.distributed as dist
-    t = torch.tensor([value], dtype=torch.float64, device="cuda")
+    dev = "cuda" if dist.get_backend() == "nccl" else "cpu"
+    t = torch.tensor([value], dtype=torch.float64, device=dev)
     dist.all_reduce(t, op=dist.ReduceOp.MAX)
     return float(t.item())
+
+
+def job_throughput(cells_per_rank, ms_per_step_local, world):
+    """Whole-job cell-updates/s: every rank advances its own replica of the
+    workload, so the job processes world x cells per step in the slowest rank's time."""
+    ms_max = barrier_and_max(ms_per_step_local, world)
+    return cells_per_rank * world / (ms_max * 1e-3), ms_max
 
 
 def cpu_baseline(prob, U, seconds=10.0):
