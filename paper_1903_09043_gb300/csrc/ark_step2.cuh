@@ -51,17 +51,23 @@ struct Step2Cfg {
     static constexpr int O_SZ = O_DZ + (VISC ? D * NT : 0);       // [D]         velocity sum of two planes (VISC)
     static constexpr int O_VF = O_SZ + (VISC ? D * NT : 0);       // [NDIR][NV]  dissipative fluxes (VISC)
     static constexpr int N_REAL = O_VF + (VISC ? NDIR * NV * NT : 0);
-    static constexpr size_t SMEM_BYTES = ((N_REAL * sizeof(Real) + 15) / 16) * 16 + NT * sizeof(double) + 4 * sizeof(double);
+    static constexpr int BRING = 8;                               // base rows kept in shared memory (split form)
+    static constexpr size_t O_BASE = ((N_REAL * sizeof(Real) + 15) / 16) * 16;
+    static constexpr size_t O_RED = O_BASE + (SPLIT ? BRING * BSTRIDE * sizeof(float) : 0);
+    static constexpr size_t SMEM_BYTES = O_RED + NT * sizeof(double) + 4 * sizeof(double);
     static_assert(NT % 32 == 0 && NT <= 1024, "block must be whole warps");
 };
 
-// Four consecutive base-table entries of one row (16-byte aligned).
+// Four consecutive base-table entries of one row.  The block keeps the rows
+// it is using in a shared ring of BRING rows (slot r & (BRING - 1)), filled one
+// plane ahead, so each read is a 16-byte shared broadcast.
 struct Base4 {
     float x, y, z, w;
 };
-__device__ __forceinline__ Base4 base4(const float* __restrict__ Bt, int group, int r)
+template <int BRING>
+__device__ __forceinline__ Base4 base4(const float* ring, int group, int r)
 {
-    const float4 v = __ldg(reinterpret_cast<const float4*>(Bt + base_index(4 * group, r)));
+    const float4 v = *reinterpret_cast<const float4*>(ring + (r & (BRING - 1)) * BSTRIDE + 4 * group);
     return Base4{v.x, v.y, v.z, v.w};
 }
 
@@ -72,7 +78,8 @@ __device__ __forceinline__ void step_block2(const StepArgs& a, const int tile, c
     constexpr int D = DIM, NF = DIM + 2, V = DIM - 1, NT = C::NT, TX = C::TX, TY = C::TY;
     static_assert(!SPLIT || sizeof(Real) == 4, "the split form stores FP32 deviations");
     Real* sm = reinterpret_cast<Real*>(smem_raw);
-    double* red = reinterpret_cast<double*>(smem_raw + ((C::N_REAL * sizeof(Real) + 15) / 16) * 16);
+    double* red = reinterpret_cast<double*>(smem_raw + C::O_RED);
+    float* const bring = reinterpret_cast<float*>(smem_raw + C::O_BASE);
 
     const Stepper<DIM, Real, SPLIT, VISC, C::TX, C::TY> S(a);
     const int t = threadIdx.x;
@@ -115,6 +122,12 @@ __device__ __forceinline__ void step_block2(const StepArgs& a, const int tile, c
 #pragma unroll
     for (int d = 0; d < 3; ++d) lam[d] = sdt[1 + d];
     const float* __restrict__ Bt = static_cast<const float*>(a.base);
+    // the base ring starts with row z0 - 2 (the first front plane); row f + 1 is
+    // loaded during plane f by the first BSTRIDE threads
+    if constexpr (SPLIT) {
+        if (t < BSTRIDE) bring[((z0 - 2) & (C::BRING - 1)) * BSTRIDE + t] = __ldg(Bt + base_index(t, z0 - 2));
+        __syncthreads();
+    }
 
     // loader position of this column (clamped into the ghost range); cell
     // offsets within a field are 32-bit (the FP32 forms need ncell < 2^32)
@@ -179,20 +192,21 @@ __device__ __forceinline__ void step_block2(const StepArgs& a, const int tile, c
         const Real fr = Real(f);
         // base rows of the planes this pass touches (split form)
         Base4 bf0{}, b10{}, b11{}, b20{}, b22{}, b23{}, b32{};
+        constexpr int BR = C::BRING;
         if constexpr (SPLIT) {
-            bf0 = base4(Bt, 0, f);        // row f:   rho0, p0, T0, H0
+            bf0 = base4<BR>(bring, 0, f);          // row f:   rho0, p0, T0, H0
             if (f >= z0) {
-                b10 = base4(Bt, 0, f - 1);  // row f-1: rho0, p0, T0, H0
-                b11 = base4(Bt, 1, f - 1);  //          R0F, Q0, DPP, DPM
+                b10 = base4<BR>(bring, 0, f - 1);  // row f-1: rho0, p0, T0, H0
+                b11 = base4<BR>(bring, 1, f - 1);  //          R0F, Q0, DPP, DPM
             } else if (f >= z0 - 1) {
-                b11 = base4(Bt, 1, f - 1);
+                b11 = base4<BR>(bring, 1, f - 1);
             }
             if (f >= z0 + 1) {
-                b22 = base4(Bt, 2, f - 2);  // row f-2: DRP, DRM, DWP, DWM
+                b22 = base4<BR>(bring, 2, f - 2);  // row f-2: DRP, DRM, DWP, DWM
                 if (f >= z0 + 2) {
-                    b20 = base4(Bt, 0, f - 2);
-                    b23 = base4(Bt, 3, f - 2);  //      DQ0
-                    b32 = base4(Bt, 2, f - 3);  // row f-3: DRP, DRM, DWP, DWM
+                    b20 = base4<BR>(bring, 0, f - 2);
+                    b23 = base4<BR>(bring, 3, f - 2);  //      DQ0
+                    b32 = base4<BR>(bring, 2, f - 3);  // row f-3: DRP, DRM, DWP, DWM
                 }
             }
         }
@@ -396,6 +410,11 @@ __device__ __forceinline__ void step_block2(const StepArgs& a, const int tile, c
         __syncthreads();
 
         // ================= H2 =================
+        // next base row into the ring (read from the next plane on)
+        float bnext = 0.f;
+        if constexpr (SPLIT) {
+            if (t < BSTRIDE && f + 1 <= nv + 1) bnext = __ldg(Bt + base_index(t, f + 1));
+        }
         // own +x / +y acoustic faces of plane f
         Real fxc[2] = {0, 0}, fyc[2] = {0, 0};
         if (f >= z0 - 1 && f <= z1) {
@@ -481,6 +500,9 @@ __device__ __forceinline__ void step_block2(const StepArgs& a, const int tile, c
                 if (sh != sh || p != p) status |= ST_NAN;
                 if (!(rho > Real(0)) || !(p > Real(0))) status |= ST_NONPHYS;
             }
+        }
+        if constexpr (SPLIT) {
+            if (t < BSTRIDE && f + 1 <= nv + 1) bring[((f + 1) & (BR - 1)) * BSTRIDE + t] = bnext;
         }
         __syncthreads();
 
