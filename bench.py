@@ -51,6 +51,16 @@ SMS, SM_GHZ = 152, 2.07
 ALU_PEAK_TFLOPS = {"f32": SMS * 128 * 2 * SM_GHZ / 1e3, "f64": SMS * 2 * 2 * SM_GHZ / 1e3}
 
 
+# 2D roofline line: the Rayleigh-Benard layer of Sec. 4.5 (2D polytrope m = 1.3,
+# chi = 1.1, box 2 x 1, Ra = 1.1 Ra_c, perturbation 1e-4 from default_rng(2)) on
+# 8192 x 4096 cells (FP32 state 0.54 GB, larger than L2).
+WORKLOAD_2D = {"workload": "rayleigh_benard_2d_8192x4096", "dim": 2, "n": [8192, 4096], "box": [2.0, 1.0],
+               "polytrope_m": 1.3, "chi": 1.1, "Ra": 1.1 * 1707.76, "Pr": 1.0, "perturbation": 1e-4, "seed": 2,
+               "bc": "periodic x; no-slip fixed-T walls y", "low_mach": 1, "cfl": 0.8}
+# path name -> (precision, workload)
+PATHS = {"f32split": ("f32split", "3d"), "f64": ("f64", "3d"), "f32": ("f32", "3d"),
+         "f32split_2d": ("f32split", "2d")}
+
 # A smaller case of the same set-up (state 160 MB FP32 / 320 MB FP64, still larger
 # than L2) used for ncu captures, which replay each launch many times.
 SMALL = dict(WORKLOAD, workload="rayleigh_benard_3d_256x256x128", n=[256, 256, 128])
@@ -58,7 +68,7 @@ SMALL = dict(WORKLOAD, workload="rayleigh_benard_3d_256x256x128", n=[256, 256, 1
 
 def make_workload(w=WORKLOAD):
     from paper_1903_09043_gb300 import inputs as I
-    return I.rayleigh_benard(3, tuple(w["n"]), m=w["polytrope_m"], chi=w["chi"], Ra=w["Ra"], Pr=w["Pr"],
+    return I.rayleigh_benard(w["dim"], tuple(w["n"]), m=w["polytrope_m"], chi=w["chi"], Ra=w["Ra"], Pr=w["Pr"],
                              amp=w["perturbation"], seed=w["seed"], low_mach=w["low_mach"], cfl=w["cfl"])
 
 
@@ -225,10 +235,10 @@ def run_reference(args, world, rank):
     print(json.dumps(line), flush=True)
 
 
-def time_path(prob, U, path, args, world, stream, sampler=None):
+def time_path(prob, U, precision, args, world, stream, sampler=None):
     import torch
     from paper_1903_09043_gb300 import ark
-    s = ark.Solver(prob, path, stream=stream.cuda_stream)
+    s = ark.Solver(prob, precision, stream=stream.cuda_stream)
     s.set_state(U)
     s.step(args.warmup)
     torch.cuda.synchronize()
@@ -337,7 +347,8 @@ def main():
     ap.add_argument("--steps", type=int, default=200)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
-    ap.add_argument("--paths", default="f32split,f64")
+    ap.add_argument("--paths", default="f32split,f64,f32split_2d",
+                    help="comma list of " + ", ".join(PATHS) + "; the first is the headline")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-batch", action="store_true")
@@ -362,18 +373,28 @@ def main():
     peaks, peak_kind = measured_peaks()
     hbm = float(peaks.get("hbm_gbs", 6800.0))
     paths = [p for p in args.paths.split(",") if p]
+    for p in paths:
+        if p not in PATHS:
+            raise SystemExit(f"unknown path {p}; choose from {', '.join(PATHS)}")
+    if args.workload == "small":
+        paths = [p for p in paths if PATHS[p][1] == "3d"]
     results = {}
     head = paths[0]
+    work2d = None
     for path in paths:
+        precision, kind = PATHS[path]
+        if kind == "2d" and work2d is None:
+            work2d = make_workload(WORKLOAD_2D)
+        pprob, pU = (prob, U) if kind == "3d" else work2d
         with torch.cuda.stream(stream):
             sampler = ClockSampler(local) if (rank == 0 and path == head) else None
-            ms, ms_max, d, shape, clocks = time_path(prob, U, path, args, world, stream, sampler)
-        cells = prob.ncells
-        B = ALG_BYTES[(path, 3)]
+            ms, ms_max, d, shape, clocks = time_path(pprob, pU, precision, args, world, stream, sampler)
+        cells = pprob.ncells
+        B = ALG_BYTES[(precision, pprob.dim)]
         achieved = cells * B / (ms * 1e-3) / 1e9
         traffic = kernel_traffic(path)
-        dt_kind = "f64" if path == "f64" else "f32"
-        flops = ALG_FLOPS[(3, prob.mu > 0 or prob.kappa > 0)]
+        dt_kind = "f64" if precision == "f64" else "f32"
+        flops = ALG_FLOPS[(pprob.dim, pprob.mu > 0 or pprob.kappa > 0)]
         tflops = cells * flops / (ms * 1e-3) / 1e12
         alu_peak = ALU_PEAK_TFLOPS[dt_kind]
         results[path] = {
@@ -384,12 +405,14 @@ def main():
                          "hbm": {"achieved": achieved, "peak": hbm, "unit": "GB/s", "frac": achieved / hbm,
                                  "alg_bytes_per_cell": B, "peak_kind": f"{peak_kind} hbm_gbs (burst copy)"}},
             "launch": shape, "final_t": d["t"], "final_dt": d["dt"], "status": d["status"], "clocks": clocks,
+            "workload": (WORKLOAD_2D if kind == "2d" else wl)["workload"],
         }
     h = results[head]
     line = {"metric": METRIC, "value": h["value"], "unit": UNIT, "n_gpus": world, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": h["ms_per_step"], "higher_is_better": True, "scaling": "weak",
             "vs_baseline": None, "dtype": h["dtype"], "data": "synthetic",
-            "config": dict(wl, path=head, l2="inputs (1.3-2.7 GB) exceed L2 (129 MB); no flush",
+            "config": dict(WORKLOAD_2D if PATHS[head][1] == "2d" else wl, path=head,
+                           l2="inputs (0.5-2.7 GB) exceed L2 (129 MB); no flush",
                            parallelism="replicas" if world > 1 else "single GPU"),
             "roofline": h["roofline"], "clocks": h["clocks"], "gpu_launches": args.steps,
             "paths": {p: {k: v for k, v in r.items() if k != "clocks"} for p, r in results.items()}}
@@ -398,7 +421,9 @@ def main():
             line["paths"]["batch"] = batch_path(args, stream, hbm)
     if rank == 0 and not args.no_e2e:
         with torch.cuda.stream(stream):
-            line["e2e"] = e2e_path(prob, U, head, args, stream)
+            hprec, hkind = PATHS[head]
+            hprob, hU = (prob, U) if hkind == "3d" else work2d
+            line["e2e"] = e2e_path(hprob, hU, hprec, args, stream)
     if rank == 0 and world == 1 and not args.no_cpu_baseline and args.workload == "full":
         line["cpu_baseline"] = cpu_baseline(prob, U)
     if world > 1:

@@ -175,12 +175,15 @@ def rb_viscosity(chi: float, m: float, gamma: float, Ra: float, Pr: float) -> Tu
 def rayleigh_benard(dim: int = 2, n: Sequence[int] = (256, 128), chi: float = 1.1, m: float = 1.3,
                     Ra: float = 1.1 * RA_CRITICAL_RIGID, Pr: float = 1.0, amp: float = 1e-4, seed: int = 2,
                     gamma: float = 5.0 / 3.0, low_mach: int = 1, cfl: float = 0.8,
-                    rng: np.random.Generator | None = None) -> Tuple[Problem, np.ndarray]:
+                    rng: np.random.Generator | None = None, roll: bool = False) -> Tuple[Problem, np.ndarray]:
     """Rayleigh-Benard layer on a polytrope (Sec. 4.5): box 2 x 1 (2D) or 2 x 2 x 1 (3D),
     periodic horizontally, no-slip fixed-temperature walls at bottom and top.
 
     Velocity perturbation: every component uniform in (-amp, amp), drawn from
-    ``numpy.random.default_rng(seed)`` (or ``rng``) over the cells in C order."""
+    ``numpy.random.default_rng(seed)`` (or ``rng``) over the cells in C order;
+    with ``roll`` (2D), instead the single convection roll pair that fits the
+    box, stream function amp sin(pi x) sin(pi y) / pi: u = amp sin(pi x) cos(pi y),
+    v = -amp cos(pi x) sin(pi y)."""
     z0 = polytrope_base(chi, m)
     mu, kappa = rb_viscosity(chi, m, gamma, Ra, Pr)
     g = -(m + 1.0)
@@ -204,10 +207,17 @@ def rayleigh_benard(dim: int = 2, n: Sequence[int] = (256, 128), chi: float = 1.
     T = z0 + 1.0 - y
     phi = -g * y
     rho, p = hydrostatic_profile(phi, T, T[0] ** (m + 1.0))
-    if rng is None:
-        rng = np.random.default_rng(seed)
-    vel = [rng.uniform(-amp, amp, size=prob.shape) for _ in range(dim)] if amp > 0 else \
-        [np.zeros(prob.shape) for _ in range(dim)]
+    if roll:
+        if dim != 2:
+            raise ValueError("roll perturbation is 2D")
+        xc = prob.centers(0)[None, :]
+        yc = y[:, None]
+        vel = [amp * np.sin(np.pi * xc) * np.cos(np.pi * yc), -amp * np.cos(np.pi * xc) * np.sin(np.pi * yc)]
+    else:
+        if rng is None:
+            rng = np.random.default_rng(seed)
+        vel = [rng.uniform(-amp, amp, size=prob.shape) for _ in range(dim)] if amp > 0 else \
+            [np.zeros(prob.shape) for _ in range(dim)]
     return prob, _assemble(prob, _bcast_profile(prob, rho), vel, _bcast_profile(prob, p))
 
 

@@ -5,6 +5,8 @@ march along y; 3D tiles are 16 x 16 and march along z), every boundary
 condition, with and without dissipation, with the low-Mach correction on and
 off; plus configurations of the paper's workloads at their full sizes.
 """
+import os
+
 import numpy as np
 import pytest
 
@@ -112,6 +114,76 @@ def test_config_rayleigh_benard_256x128():
     V, d = gpu_run(prob, U, 1000)
     assert max_error(prob, V, ref) <= F64_TOL
     assert d["t"] == pytest.approx(t, rel=1e-13)
+
+
+def _growth_series(prob, U, steps, every, runner):
+    ts, vs = [], []
+    V = U
+    for _ in range(steps // every):
+        V, d = runner(V, every)
+        ts.append(d["t"])
+        vs.append(d["mean_abs_v_last"])
+    ts, vs = np.array(ts), np.array(vs)
+    half = len(ts) // 2
+    return V, float(np.polyfit(ts[half:], np.log(vs[half:]), 1)[0]), vs
+
+
+def test_rayleigh_benard_onset_growth_rate_matches_oracle():
+    """2D Rayleigh-Benard 256 x 128 (Sec. 4.5), roll-pair perturbation, 2e4 steps
+    at 5 Ra_c with the low-Mach correction: the convective mode grows, and the
+    GPU's growth rate, mean |v| history and final state equal the oracle's."""
+    prob, U = I.rayleigh_benard(2, (256, 128), Ra=5.0 * I.RA_CRITICAL_RIGID, roll=True)
+    ark = _ark()
+
+    clock = [0.0]
+
+    def oracle_runner(V, n):
+        W, t = O.run(prob, V, n)
+        clock[0] += t
+        d = O.diagnostics(prob, W)
+        return W, {"t": clock[0], "mean_abs_v_last": d["mean_abs_v_last"]}
+
+    O.set_threads(os.cpu_count() or 1)
+    try:
+        ref, rate_ref, v_ref = _growth_series(prob, U, 20000, 2000, oracle_runner)
+    finally:
+        O.set_threads(1)
+    with ark.Solver(prob, "f64", stream=_stream()) as s:
+        s.set_state(U)
+
+        def gpu_runner(V, n):
+            s.step(n)
+            return None, s.diagnostics(check=False)
+
+        _, rate, v = _growth_series(prob, U, 20000, 2000, gpu_runner)
+        V = s.get_state()
+    assert rate_ref > 0.0
+    assert rate == pytest.approx(rate_ref, rel=1e-9)
+    np.testing.assert_allclose(v, v_ref, rtol=1e-9)
+    assert max_error(prob, V, ref) <= F64_TOL
+
+
+def test_rayleigh_benard_growth_rate_rises_with_ra_and_with_theta():
+    """Near onset the growth rate of the roll increases with Ra, and the low-Mach
+    correction (Eq. 16) removes numerical damping: the rate with theta exceeds
+    the rate without it at the same Ra (Sec. 4.5 and Sec. 2.1.5)."""
+    ark = _ark()
+    rates = {}
+    for ratio in (2.0, 5.0):
+        for low_mach in (1, 0):
+            prob, U = I.rayleigh_benard(2, (256, 128), Ra=ratio * I.RA_CRITICAL_RIGID, roll=True, low_mach=low_mach)
+            with ark.Solver(prob, "f64", stream=_stream()) as s:
+                s.set_state(U)
+
+                def gpu_runner(V, n):
+                    s.step(n)
+                    return None, s.diagnostics(check=False)
+
+                _, rates[ratio, low_mach], _ = _growth_series(prob, U, 20000, 1000, gpu_runner)
+    assert rates[5.0, 1] > rates[2.0, 1]
+    assert rates[5.0, 0] > rates[2.0, 0]
+    assert rates[2.0, 1] > rates[2.0, 0] + 0.05
+    assert rates[5.0, 1] > rates[5.0, 0] + 0.05
 
 
 def _sample_points(prob, rng, k):
