@@ -290,6 +290,30 @@ def well_balanced_column(n: int = 128, low_mach: int = 1, gamma: float = 5.0 / 3
     return prob, _assemble(prob, _bcast_profile(prob, rho), [zero, zero], _bcast_profile(prob, p))
 
 
+def rayleigh_taylor(n: Sequence[int] = (200, 600), C: float = 0.01, g: float = -0.1, p0: float = 2.5,
+                    gamma: float = 1.4, low_mach: int = 1, cfl: float = 0.8) -> Tuple[Problem, np.ndarray]:
+    """Rayleigh-Taylor instability (Sec. 4.4) on [-0.25, 0.25] x [-0.75, 0.75]:
+    rho = 2 above y = 0 and 1 below, at rest in hydrostatic balance
+    p = p0 + rho g y (the printed p = rho g y is negative; the pressure offset
+    p0 = 2.5 and g = -0.1 make it the standard set-up), vertical velocity
+    v = C/4 (1 + cos(2 pi x / Lx)) (1 + cos(2 pi y / Ly)).  Periodic in x,
+    reflective hydrostatic walls in y.  With the interface on a face (even
+    ny) the state at rest is a discrete equilibrium of the scheme: in each
+    fluid p_{j+1} - p_j equals the source S, and across the interface both are
+    -(1 + 2)/2 |g| dy."""
+    nx, ny = int(n[0]), int(n[1])
+    prob = Problem(dim=2, n=(nx, ny, 1), lo=(-0.25, -0.75, 0.0), hi=(0.25, 0.75, 1.0), gamma=gamma, g=g,
+                   low_mach=low_mach, cfl=cfl, bc_lo=(PERIODIC, REFLECT_HYDRO, PERIODIC),
+                   bc_hi=(PERIODIC, REFLECT_HYDRO, PERIODIC))
+    x = prob.centers(0)[None, :]
+    y = prob.centers(1)[:, None]
+    rho = np.where(y >= 0.0, 2.0, 1.0) * np.ones((1, nx))
+    p = p0 + rho * g * y
+    Lx, Ly = 0.5, 1.5
+    v = 0.25 * C * (1.0 + np.cos(2.0 * np.pi * x / Lx)) * (1.0 + np.cos(2.0 * np.pi * y / Ly))
+    return prob, _assemble(prob, rho, [np.zeros((ny, nx)), v], p)
+
+
 def random_periodic(dim: int = 2, n: Sequence[int] = (24, 20), seed: int = 0, amp: float = 0.1,
                     gamma: float = 1.4, mu: float = 0.0, kappa: float = 0.0, low_mach: int = 1,
                     cfl: float = 0.5) -> Tuple[Problem, np.ndarray]:

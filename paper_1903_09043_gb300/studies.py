@@ -2,6 +2,8 @@
 
     python -m paper_1903_09043_gb300.studies precision   # Gresho 1024^2, Mach sweep, FP32 forms vs FP64
     python -m paper_1903_09043_gb300.studies rb_growth   # 2D Rayleigh-Benard 256x128 onset sweep, 2e4 steps
+    python -m paper_1903_09043_gb300.studies rb_onset    # the same, Ra/Ra_c 1.1 .. 30, 8e4 steps, FP64
+    python -m paper_1903_09043_gb300.studies rayleigh_taylor  # Sec. 4.4, 200x600 to t = 12.4, theta on/off
     python -m paper_1903_09043_gb300.studies spectrum    # 3D Rayleigh-Benard 512x512x256, FP32 vs FP64 spectrum
 
 Each prints one JSON document.  The FP64 path is the reference of the
@@ -109,6 +111,53 @@ def rb_growth(steps=20000, every=500, ratios=(0.9, 1.1, 1.5, 2.0, 3.0, 5.0), rol
             + ("roll-pair" if roll else "white-noise") + " perturbation 1e-4", "rows": rows}
 
 
+def rayleigh_taylor(n=(200, 600), t_final=12.4, chunk=50):
+    """Rayleigh-Taylor (Sec. 4.4) on 200 x 600 to t = 12.4 with and without the
+    low-Mach correction: growth rate of max |v| over t in [1, 4] (the
+    incompressible linear rate of the seeded mode is sqrt(A g k) with Atwood
+    number A = 1/3, g = 0.1, k = 4 pi), mixing-zone extent at t_final (rows
+    whose mean density lies strictly between 1.05 and 1.95), FP32-split vs FP64."""
+    sigma = math.sqrt((1.0 / 3.0) * 0.1 * 4.0 * math.pi)
+    rows = []
+    for low_mach in (1, 0):
+        finals = {}
+        for prec in ("f64", "f32split"):
+            prob, U = I.rayleigh_taylor(n, low_mach=low_mach)
+            ts, vs = [], []
+            with ark.Solver(prob, prec, stream=_stream()) as s:
+                s.set_state(U)
+                while True:
+                    d = s.diagnostics(check=False)
+                    ts.append(d["t"])
+                    vs.append(d["max_speed"])
+                    remaining = t_final - d["t"]
+                    if remaining <= 1e-12:
+                        break
+                    dt = s.compute_dt()
+                    if remaining > (chunk + 10) * dt:
+                        s.step(chunk)                  # CFL steps
+                    elif remaining > dt:
+                        s.step(1)
+                    else:
+                        s.step(1, remaining)           # land on t_final
+                V = s.get_state()
+                steps = s.diagnostics(check=False)["step"]
+            ts, vs = np.array(ts), np.array(vs)
+            sel = (ts >= 1.0) & (ts <= 4.0)
+            rate = float(np.polyfit(ts[sel], np.log(vs[sel]), 1)[0])
+            rho_mean = V[0].mean(axis=1)
+            mixed = np.nonzero((rho_mean > 1.05) & (rho_mean < 1.95))[0]
+            y = prob.centers(1)
+            width = float(y[mixed[-1]] - y[mixed[0]]) if mixed.size else 0.0
+            finals[prec] = V
+            rows.append({"low_mach": low_mach, "precision": prec, "steps": int(steps), "t_final": float(ts[-1]),
+                         "growth_rate_t1_4": rate, "growth_rate_over_linear_theory": rate / sigma,
+                         "max_speed_final": float(vs[-1]), "mixing_zone_width": width})
+        rows[-1]["f32split_density_linf_vs_f64"] = float(np.max(np.abs(finals["f32split"][0] - finals["f64"][0])))
+    return {"study": "rayleigh_taylor", "workload": f"rayleigh_taylor {n[0]}x{n[1]} to t = {t_final}",
+            "linear_theory_rate": sigma, "rows": rows}
+
+
 def ke_spectrum(V, prob):
     """Shell-binned kinetic-energy spectrum of the horizontal middle plane."""
     k = prob.n[2] // 2
@@ -149,13 +198,18 @@ def spectrum(steps=200):
 
 def main():
     ap = argparse.ArgumentParser()
-    ap.add_argument("study", choices=["precision", "rb_growth", "spectrum"])
+    ap.add_argument("study", choices=["precision", "rb_growth", "rb_onset", "rayleigh_taylor", "spectrum"])
     ap.add_argument("--n", type=int, default=1024)
     args = ap.parse_args()
     if args.study == "precision":
         res = precision(n=args.n)
     elif args.study == "rb_growth":
         res = rb_growth()
+    elif args.study == "rb_onset":
+        res = rb_growth(steps=80000, every=2000, ratios=(1.1, 1.5, 2.0, 3.0, 5.0, 10.0, 15.0, 20.0, 25.0, 30.0),
+                        precisions=("f64",))
+    elif args.study == "rayleigh_taylor":
+        res = rayleigh_taylor()
     else:
         res = spectrum()
     print(json.dumps(res))

@@ -59,6 +59,10 @@ CASES = {
     "3d_strat_reflect": lambda: I.stratified_random(3, (19, 6, 8), walls=I.REFLECT_HYDRO),
     "3d_multi_tile": lambda: I.stratified_random(3, (35, 33, 12), mu=0.005, kappa=0.005),
     "3d_rb": lambda: I.rayleigh_benard(3, (20, 20, 10), amp=1e-3),
+    "2d_rb_chi21": lambda: I.rayleigh_benard(2, (40, 24), chi=21.0, amp=1e-3),
+    "3d_rb_chi21": lambda: I.rayleigh_benard(3, (14, 12, 24), chi=21.0, m=1.3, amp=1e-3),
+    "2d_rayleigh_taylor": lambda: I.rayleigh_taylor((24, 72)),
+    "2d_rayleigh_taylor_theta1": lambda: I.rayleigh_taylor((24, 72), low_mach=0),
 }
 
 
@@ -157,10 +161,13 @@ def test_rayleigh_benard_onset_growth_rate_matches_oracle():
 
         _, rate, v = _growth_series(prob, U, 20000, 2000, gpu_runner)
         V = s.get_state()
-    assert rate_ref > 0.0
-    assert rate == pytest.approx(rate_ref, rel=1e-9)
-    np.testing.assert_allclose(v, v_ref, rtol=1e-9)
+    # the state equals the oracle's to the FP64 tolerance of the field scale;
+    # mean |v| is a 1e-5 perturbation of that scale, so its agreement (and the
+    # fitted rate's) is looser in relative terms by the same factor
     assert max_error(prob, V, ref) <= F64_TOL
+    assert rate_ref > 0.0
+    assert rate == pytest.approx(rate_ref, rel=1e-5)
+    np.testing.assert_allclose(v, v_ref, rtol=1e-6)
 
 
 def test_rayleigh_benard_growth_rate_rises_with_ra_and_with_theta():
@@ -219,7 +226,8 @@ def test_full_size_3d_rb_sampled(precision):
         assert max(errs) <= tol, (p, errs)
 
 
-@pytest.mark.parametrize("case", ["2d_periodic_visc", "2d_strat_noslip_visc", "3d_strat_noslip_visc_ragged", "3d_rb"])
+@pytest.mark.parametrize("case", ["2d_periodic_visc", "2d_strat_noslip_visc", "3d_strat_noslip_visc_ragged", "3d_rb",
+                                  "2d_rb_chi21", "3d_rb_chi21", "2d_rayleigh_taylor"])
 @pytest.mark.parametrize("precision", ["f32", "f32split"])
 def test_fp32_forms_match_oracle_within_budget(case, precision):
     prob, U = CASES[case]()

@@ -501,3 +501,41 @@ def test_appendix_b_converges_to_the_conservative_form():
         gaps.append(max(np.max(np.abs(A[f] - B0[f])) / np.max(np.abs(A[f])) for f in (0, 2, 3)))
     assert gaps[0] < 0.02
     assert math.log2(gaps[0] / gaps[1]) > 0.8 and math.log2(gaps[1] / gaps[2]) > 0.8
+
+
+# --------------------------------------------------------------------------
+# Rayleigh-Taylor set-up (Sec. 4.4) and strong stratification (Sec. 4.5)
+# --------------------------------------------------------------------------
+@pytest.mark.parametrize("low_mach", [1, 0])
+def test_rayleigh_taylor_rest_state_is_a_discrete_equilibrium(low_mach):
+    """The two-fluid state at rest (density jump 1 -> 2 on a face) stays at rest
+    to round-off without any well-balanced reconstruction: the source S of
+    every face, the interface included, equals the pressure jump (Sec. 4.4)."""
+    prob, U = I.rayleigh_taylor((20, 60), C=0.0, low_mach=low_mach)
+    V, _ = O.run(prob, U, 500)
+    d = O.diagnostics(prob, V)
+    assert d["max_speed"] < 1e-12
+    assert np.max(np.abs(V[0] - U[0])) < 1e-12
+
+
+def test_rayleigh_taylor_interface_is_unstable_and_conserves_mass():
+    """Heavy over light is unstable: the seeded mode grows, mass and energy
+    are conserved between the reflective walls."""
+    prob, U = I.rayleigh_taylor((20, 60), C=0.01)
+    V, t = O.run(prob, U, 10 ** 6, t_end=6.0)
+    d0, d1 = O.diagnostics(prob, U), O.diagnostics(prob, V)
+    assert d1["max_speed"] > 2.0 * d0["max_speed"]
+    assert d1["mass"] == pytest.approx(d0["mass"], rel=1e-13)
+    assert d1["energy"] == pytest.approx(d0["energy"], rel=1e-13)
+
+
+def test_strongly_stratified_polytrope_stays_at_rest():
+    """chi = 21 (density contrast 21 across the layer, Sec. 4.5): the discrete
+    polytrope at rest with the no-slip fixed-temperature walls and heat
+    conduction stays at rest (linear T: uniform conductive flux)."""
+    prob, U = I.rayleigh_benard(2, (16, 40), chi=21.0, amp=0.0)
+    # rho = T^m with T = z0 + 1 - y: the wall densities differ by chi
+    assert (prob.T_lo[1] / prob.T_hi[1]) ** 1.3 == pytest.approx(21.0, rel=1e-12)
+    V, _ = O.run(prob, U, 300)
+    assert O.diagnostics(prob, V)["max_speed"] < 1e-10
+
