@@ -71,6 +71,46 @@ __device__ __forceinline__ Base4 base4(const float* ring, int group, int r)
     return Base4{v.x, v.y, v.z, v.w};
 }
 
+// Field-parallel arithmetic on pairs of FP32 values (Blackwell's packed FP32x2
+// instructions: one issue slot for two lanes' worth of operations).
+__device__ __forceinline__ float2 pr(float a, float b) { return make_float2(a, b); }
+// c[k] = a[k] * s, k < N
+template <int N>
+__device__ __forceinline__ void scale_n(float* c, const float* a, float s)
+{
+    const float2 s2 = pr(s, s);
+#pragma unroll
+    for (int k = 0; k + 1 < N; k += 2) {
+        const float2 r = __fmul2_rn(pr(a[k], a[k + 1]), s2);
+        c[k] = r.x;
+        c[k + 1] = r.y;
+    }
+    if constexpr (N % 2) c[N - 1] = a[N - 1] * s;
+}
+// c[k] = a[k] * s - l0 (b0[k] - m0[k]) [- l1 (b1[k] - m1[k])] - l2 (b2[k] - m2[k]), k < N
+template <int N, bool TWO>
+__device__ __forceinline__ void flux_update_n(float* c, const float* a, float s, float l0, const float* b0,
+                                              const float* m0, float l1, const float* b1, const float* m1, float l2,
+                                              const float* b2, const float* m2)
+{
+    const float2 s2 = pr(s, s), n0 = pr(-l0, -l0), n1 = pr(-l1, -l1), n2 = pr(-l2, -l2), one = pr(-1.f, -1.f);
+#pragma unroll
+    for (int k = 0; k + 1 < N; k += 2) {
+        float2 r = __fmul2_rn(pr(a[k], a[k + 1]), s2);
+        r = __ffma2_rn(n0, __ffma2_rn(pr(m0[k], m0[k + 1]), one, pr(b0[k], b0[k + 1])), r);
+        if constexpr (TWO) r = __ffma2_rn(n1, __ffma2_rn(pr(m1[k], m1[k + 1]), one, pr(b1[k], b1[k + 1])), r);
+        r = __ffma2_rn(n2, __ffma2_rn(pr(m2[k], m2[k + 1]), one, pr(b2[k], b2[k + 1])), r);
+        c[k] = r.x;
+        c[k + 1] = r.y;
+    }
+    if constexpr (N % 2) {
+        constexpr int k = N - 1;
+        float r = a[k] * s - l0 * (b0[k] - m0[k]);
+        if constexpr (TWO) r -= l1 * (b1[k] - m1[k]);
+        c[k] = r - l2 * (b2[k] - m2[k]);
+    }
+}
+
 template <int DIM, typename Real, bool SPLIT, bool VISC, int R2X, int R2Y>
 __device__ __forceinline__ void step_block2(const StepArgs& a, const int tile, const int chunk, unsigned char* smem_raw)
 {
@@ -279,10 +319,14 @@ __device__ __forceinline__ void step_block2(const StepArgs& a, const int tile, c
             if (a.energy_form) W_t += lam[V] * Real(0.5) * (zfu[0] * zfu[2] + zfl[0] * zfl[2]);   // (uS)_i, Appendix B
             const Real L = Real(1) + ell;
             const Real rL = rcp(L);
-            tlB[0] = SPLIT ? (cp.drho - Real(b10.x) * ell) * rL : cp.drho * rL;
+            {
+                Real pre[NF];
+                pre[0] = SPLIT ? cp.drho - Real(b10.x) * ell : cp.drho;
 #pragma unroll
-            for (int d = 0; d < D; ++d) tlB[1 + d] = m_t[d] * rL;
-            tlB[D + 1] = W_t * rL;
+                for (int d = 0; d < D; ++d) pre[1 + d] = m_t[d];
+                pre[D + 1] = W_t;
+                scale_n<NF>(tlB, pre, rL);
+            }
             tlB[NF] = L;
             const bool valid = (x0 + lx) >= 0 && (x0 + lx) < nx && (D == 2 || ((y0 + ly) >= 0 && (y0 + ly) < ny)) &&
                                q1 >= 0 && q1 < nv;
@@ -374,20 +418,22 @@ __device__ __forceinline__ void step_block2(const StepArgs& a, const int tile, c
         if (f >= z0 + 2) {
             if (xfT) {
                 const bool upL = fx2 >= Real(0);
+                Real up[NF];
 #pragma unroll
-                for (int k = 0; k < NF; ++k) {
-                    tfx[k] = (upL ? tlA[k] : TL[k * NT + SX]) * fx2;
-                    TF[k * NT] = tfx[k];
-                }
+                for (int k = 0; k < NF; ++k) up[k] = upL ? tlA[k] : TL[k * NT + SX];
+                scale_n<NF>(tfx, up, fx2);
+#pragma unroll
+                for (int k = 0; k < NF; ++k) TF[k * NT] = tfx[k];
             }
             if constexpr (D == 3) {
                 if (yfT) {
                     const bool upL = fy2 >= Real(0);
+                    Real up[NF];
 #pragma unroll
-                    for (int k = 0; k < NF; ++k) {
-                        tfy[k] = (upL ? tlA[k] : TL[k * NT + SY]) * fy2;
-                        TF[(NF + k) * NT] = tfy[k];
-                    }
+                    for (int k = 0; k < NF; ++k) up[k] = upL ? tlA[k] : TL[k * NT + SY];
+                    scale_n<NF>(tfy, up, fy2);
+#pragma unroll
+                    for (int k = 0; k < NF; ++k) TF[(NF + k) * NT] = tfy[k];
                 }
             }
         }
@@ -398,8 +444,10 @@ __device__ __forceinline__ void step_block2(const StepArgs& a, const int tile, c
         for (int k = 0; k < NF; ++k) zt_hi[k] = 0;
         if (f >= z0 + 1 && inT) {
             const bool upL = us_hi >= Real(0);
+            Real up[NF];
 #pragma unroll
-            for (int k = 0; k < NF; ++k) zt_hi[k] = (upL ? tlA[k] : tlB[k]) * us_hi;
+            for (int k = 0; k < NF; ++k) up[k] = upL ? tlA[k] : tlB[k];
+            scale_n<NF>(zt_hi, up, us_hi);
             if constexpr (SPLIT) {
                 if (!upL) {
                     zt_hi[0] += Real(b22.x) * us_hi;
@@ -455,12 +503,11 @@ __device__ __forceinline__ void step_block2(const StepArgs& a, const int tile, c
             const int q = f - 2;
             const Real L = tlA[NF];
             Real nb[NF];
+            Real tmx[NF], tmy[NF];
 #pragma unroll
             for (int k = 0; k < NF; ++k) {
-                Real acc = tlA[k] * L;
-                acc -= lam[0] * (tfx[k] - TF[k * NT - SX]);
-                if constexpr (D == 3) acc -= lam[1] * (tfy[k] - TF[(NF + k) * NT - SY]);
-                nb[k] = acc;
+                tmx[k] = TF[k * NT - SX];
+                tmy[k] = D == 3 ? TF[(NF + k) * NT - SY] : Real(0);
             }
             Real lowfix[NF];
 #pragma unroll
@@ -474,8 +521,7 @@ __device__ __forceinline__ void step_block2(const StepArgs& a, const int tile, c
                     lowfix[D + 1] -= Real(b32.z) * us_lo;
                 }
             }
-#pragma unroll
-            for (int k = 0; k < NF; ++k) nb[k] -= lam[V] * (zt_hi[k] - lowfix[k]);
+            flux_update_n<NF, D == 3>(nb, tlA, L, lam[0], tfx, tmx, lam[1], tfy, tmy, lam[V], zt_hi, lowfix);
             if constexpr (VISC) {
 #pragma unroll
                 for (int k = 0; k < C::NV; ++k) {
