@@ -85,17 +85,59 @@ struct Row {
     Real rho0, p0, T0, phi;
 };
 
-// Reciprocal and square root.  FP64: the exact (correctly rounded) operations,
-// as the oracle uses.  FP32: the hardware approximations (within 2 ulp), one
-// special-function instruction each instead of the IEEE refinement sequences;
-// the FP32 forms' error budget is several ulp per step.
-__device__ __forceinline__ double rcp(double x) { return 1.0 / x; }
+// Reciprocal and square root.
+// FP64: Newton-Raphson iteration (the textbook scheme for reciprocals and
+// reciprocal square roots, e.g. Markstein, IBM J. Res. Dev. 34 (1990)) from
+// the hardware's approximate FP64 seeds (rcp.approx.ftz.f64 and
+// rsqrt.approx.ftz.f64, relative error below 2^-22).  Each iteration squares
+// the relative error, so two leave it below 2^-88 and the result is within one
+// ulp of the correctly rounded value, at a fraction of the FP64-pipe work of
+// the IEEE division and square root.  Arguments are positive normal numbers
+// (densities, L~, gamma p / rho); zero, infinite or NaN arguments give NaN,
+// which the step's status word reports.
+// FP32: the hardware approximations (within 2 ulp), one special-function
+// instruction each; the FP32 forms' error budget is several ulp per step.
+__device__ __forceinline__ double rcp_seed(double x)
+{
+#ifdef __CUDA_ARCH__
+    double y;
+    asm("rcp.approx.ftz.f64 %0, %1;" : "=d"(y) : "d"(x));
+    return y;
+#else
+    return 1.0 / x;   // host-side parsing of device code only
+#endif
+}
+__device__ __forceinline__ double rsqrt_seed(double q)
+{
+#ifdef __CUDA_ARCH__
+    double y;
+    asm("rsqrt.approx.ftz.f64 %0, %1;" : "=d"(y) : "d"(q));
+    return y;
+#else
+    return 1.0 / sqrt(q);
+#endif
+}
+__device__ __forceinline__ double rcp(double x)
+{
+    double y = rcp_seed(x);
+    double e = fma(-x, y, 1.0);   // relative error of y
+    y = fma(y, e, y);
+    e = fma(-x, y, 1.0);
+    return fma(y, e, y);
+}
 __device__ __forceinline__ float rcp(float x) { return __fdividef(1.0f, x); }
 // c = sqrt(q) and 1 / c together
 __device__ __forceinline__ void sqrt_rsqrt(double q, double& c, double& rc)
 {
-    c = sqrt(q);
-    rc = 1.0 / c;
+    double y = rsqrt_seed(q);
+    double e = fma(-q * y, y, 1.0);   // 1 - q y^2
+    y = fma(0.5 * y, e, y);            // y (1 + e / 2)
+    e = fma(-q * y, y, 1.0);
+    y = fma(0.5 * y, e, y);
+    double s = q * y;                  // sqrt(q), then one correction on the residual q - s^2
+    s = fma(fma(-s, s, q), 0.5 * y, s);
+    c = s;
+    rc = fma(y, fma(-s, y, 1.0), y);   // 1 / c, one reciprocal correction on the rounded c
 }
 __device__ __forceinline__ void sqrt_rsqrt(float q, float& c, float& rc)
 {
@@ -109,6 +151,20 @@ __device__ __forceinline__ float vmax(float a, float b) { return fmaxf(a, b); }
 __device__ __forceinline__ double vmax(double a, double b) { return fmax(a, b); }
 __device__ __forceinline__ float vmin(float a, float b) { return fminf(a, b); }
 __device__ __forceinline__ double vmin(double a, double b) { return fmin(a, b); }
+// Maximum and minimum of non-negative values (rho c, 1/(rho c), 1/c, rates).
+// For FP64 they compare the bit patterns as integers, which orders
+// non-negative doubles as their values do and keeps the comparison off the
+// FP64 pipe; a NaN operand wins the maximum (it is reported by the status word).
+__device__ __forceinline__ float pmax(float a, float b) { return fmaxf(a, b); }
+__device__ __forceinline__ float pmin(float a, float b) { return fminf(a, b); }
+__device__ __forceinline__ double pmax(double a, double b)
+{
+    return __longlong_as_double(max(__double_as_longlong(a), __double_as_longlong(b)));
+}
+__device__ __forceinline__ double pmin(double a, double b)
+{
+    return __longlong_as_double(min(__double_as_longlong(a), __double_as_longlong(b)));
+}
 __device__ __forceinline__ float vabs(float a) { return fabsf(a); }
 __device__ __forceinline__ double vabs(double a) { return fabs(a); }
 __device__ __forceinline__ float vsqrt(float a) { return sqrtf(a); }
@@ -261,11 +317,11 @@ __device__ __forceinline__ Real wave_rate(const Real* b, const Row<Real>& w, Rea
     for (int d = 0; d < D; ++d) sh += (vabs(uu[d]) + cs) * invdx[d];
     if constexpr (VISC) {
         const Real nu = Real(4.0 / 3.0) * mu * rr, chi = kappa * gm1 * rr;
-        const Real dm = vmax(nu, chi);
+        const Real dm = pmax(nu, chi);
         Real sp = Real(0);
 #pragma unroll
         for (int d = 0; d < D; ++d) sp += Real(2) * dm * invdx[d] * invdx[d];
-        sh = vmax(sh, sp);
+        sh = pmax(sh, sp);
     }
     return sh;
 }
@@ -390,11 +446,11 @@ __device__ __forceinline__ void acoustic_face(Real uL, Real uR, Real dpL, Real d
                                               Real rzR, Real rcL, Real rcR, Real pjump_base, Real dS, Real K,
                                               Real halfInvK, int low_mach, Real& ustar, Real& dPi)
 {
-    const Real a = K * vmax(zL, zR);
-    const Real inv2a = halfInvK * vmin(rzL, rzR);
+    const Real a = K * pmax(zL, zR);
+    const Real inv2a = halfInvK * pmin(rzL, rzR);
     ustar = Real(0.5) * (uL + uR) - (pjump_base + dpR - dpL - dS) * inv2a;
     Real theta = Real(1);
-    if (low_mach) theta = vmin(vabs(ustar) * vmin(rcL, rcR), Real(1));
+    if (low_mach) theta = pmin(vabs(ustar) * pmin(rcL, rcR), Real(1));
     dPi = Real(0.5) * (dpL + dpR) - Real(0.5) * a * theta * (uR - uL);
 }
 
