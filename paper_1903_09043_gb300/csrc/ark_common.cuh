@@ -65,6 +65,7 @@ struct StepArgs {
     // that no kernel converts between precisions (conversions run on GB300's
     // FP64 pipe, 1/64 of its FP32 rate)
     float fK, fhalfInvK, fmu, fkappa, feta, fgamma, fgm1, fphi_g, fphi_lo, fphi_dv, finvdx[3];
+    float fdphi;            // Phi_{r+1} - Phi_r = -g dz, formed in FP64 (uniform g)
     double dK, dhalfInvK, deta, dinvdx[3];
 };
 
@@ -87,6 +88,7 @@ inline void fill_constants(StepArgs& a)
     a.fphi_lo = (float)a.lo_v;
     a.fphi_dv = (float)a.dx[V];
     for (int d = 0; d < 3; ++d) a.finvdx[d] = (float)a.dinvdx[d];
+    a.fdphi = (float)(-a.g * a.dx[V]);
 }
 
 }  // namespace ark

@@ -318,10 +318,10 @@ __device__ __forceinline__ Real wave_rate(const Real* b, const Row<Real>& w, Rea
     if constexpr (VISC) {
         const Real nu = Real(4.0 / 3.0) * mu * rr, chi = kappa * gm1 * rr;
         const Real dm = pmax(nu, chi);
-        Real sp = Real(0);
+        Real s2 = Real(0);   // sum_d 2 / dx_d^2 (loop-invariant)
 #pragma unroll
-        for (int d = 0; d < D; ++d) sp += Real(2) * dm * invdx[d] * invdx[d];
-        sh = pmax(sh, sp);
+        for (int d = 0; d < D; ++d) s2 += Real(2) * invdx[d] * invdx[d];
+        sh = pmax(sh, dm * s2);
     }
     return sh;
 }

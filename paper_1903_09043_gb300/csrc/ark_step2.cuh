@@ -288,8 +288,8 @@ __device__ __forceinline__ void step_block2(const StepArgs& a, const int tile, c
         // own z face (f-1, f)
         Real zfu[3] = {0, 0, 0};
         if (f >= z0 - 1 && inR1) {
-            const Real dphi = S.phi.at(fr) - S.phi.at(fr - Real(1));
-            zfu[2] = Real(-0.5) * (cp.drho + cc.drho) * dphi;
+            // Phi jump across the face: -g dz for uniform g, rounded once from FP64
+            zfu[2] = Real(-0.5) * (cp.drho + cc.drho) * Real(a.fdphi);
             acoustic_face<Real>(vt1[V], cc.u[V], cp.dp, cc.dp, cp.z, zc, cp.rz, rzc, cp.rc, rcc,
                                 SPLIT ? Real(b11.x) : Real(0), zfu[2], kc.K, kc.halfInvK, a.low_mach, zfu[0], zfu[1]);
         }
@@ -338,43 +338,50 @@ __device__ __forceinline__ void step_block2(const StepArgs& a, const int tile, c
 #pragma unroll
         for (int k = 0; k < C::NV; ++k) zv_new[k] = 0;
         if constexpr (VISC) {
-            const Real mu = kc.mu, kappa = kc.kappa, eta = kc.eta;
+            // tau = mu (grad u + grad u^T) + eta (div u) I and the work and heat
+            // fluxes of Sec. 2.2 at one face; only the derivatives tau and
+            // div u need are formed.  qt = dx^-1 / 4 scales the averaged
+            // tangential differences (an exact power-of-two factor).
+            const Real mu = kc.mu, eta = kc.eta, mu2 = Real(2) * kc.mu;
+            Real qt[3], kinv[3];
+#pragma unroll
+            for (int d = 0; d < 3; ++d) {
+                qt[d] = Real(0.25) * kc.invdx[d];
+                kinv[d] = kc.kappa * kc.invdx[d];
+            }
             if (f >= z0 + 2) {
                 auto face = [&](auto dirc) {
                     constexpr int dir = decltype(dirc)::value;
                     constexpr int sh = dir == 0 ? SX : SY;
-                    Real grad[3][3];
+                    Real vj[C::NVT];
 #pragma unroll
-                    for (int aa = 0; aa < 3; ++aa)
+                    for (int q = 0; q < C::NVT; ++q) vj[q] = VT[q * NT + sh];
+                    Real gn[D];                       // d u_q / d x_dir
 #pragma unroll
-                        for (int qq = 0; qq < 3; ++qq) grad[aa][qq] = 0;
-#pragma unroll
-                    for (int qq = 0; qq < D; ++qq) grad[dir][qq] = (VT[qq * NT + sh] - vt2[qq]) * kc.invdx[dir];
+                    for (int q = 0; q < D; ++q) gn[q] = (vj[q] - vt2[q]) * kc.invdx[dir];
+                    Real tau[D];
+                    Real divu = gn[dir];
                     if constexpr (D == 3) {
                         constexpr int tt = 1 - dir;
                         constexpr int st = tt == 0 ? SX : SY;
-#pragma unroll
-                        for (int qq = 0; qq < D; ++qq)
-                            grad[tt][qq] = Real(0.25) *
-                                           ((VT[qq * NT + st] - VT[qq * NT - st]) +
-                                            (VT[qq * NT + sh + st] - VT[qq * NT + sh - st])) *
-                                           kc.invdx[tt];
+                        auto tder = [&](int q) {
+                            return ((VT[q * NT + st] - VT[q * NT - st]) + (VT[q * NT + sh + st] - VT[q * NT + sh - st])) *
+                                   qt[tt];
+                        };
+                        tau[tt] = mu * (gn[tt] + tder(dir));
+                        divu += tder(tt);
                     }
-#pragma unroll
-                    for (int qq = 0; qq < D; ++qq)
-                        grad[V][qq] = Real(0.25) * (DZ[qq * NT] + DZ[qq * NT + sh]) * kc.invdx[V];
-                    Real divu = 0;
-#pragma unroll
-                    for (int aa = 0; aa < D; ++aa) divu += grad[aa][aa];
+                    const Real gv_dir = (DZ[dir * NT] + DZ[dir * NT + sh]) * qt[V];
+                    divu += (DZ[V * NT] + DZ[V * NT + sh]) * qt[V];
+                    tau[V] = mu * (gn[V] + gv_dir);
+                    tau[dir] = mu2 * gn[dir] + eta * divu;
                     Real work = 0;
 #pragma unroll
-                    for (int qq = 0; qq < D; ++qq) {
-                        Real tau = mu * (grad[dir][qq] + grad[qq][dir]);
-                        if (qq == dir) tau += eta * divu;
-                        work += tau * Real(0.5) * (vt2[qq] + VT[qq * NT + sh]);
-                        VF[(dir * C::NV + qq) * NT] = tau;
+                    for (int q = 0; q < D; ++q) {
+                        work += tau[q] * (vt2[q] + vj[q]);
+                        VF[(dir * C::NV + q) * NT] = tau[q];
                     }
-                    VF[(dir * C::NV + D) * NT] = work + kappa * (VT[D * NT + sh] - vt2[D]) * kc.invdx[dir];
+                    VF[(dir * C::NV + D) * NT] = Real(0.5) * work + (vj[D] - vt2[D]) * kinv[dir];
                 };
                 if (xfT) face(IC<0>{});
                 if constexpr (D == 3) {
@@ -382,32 +389,25 @@ __device__ __forceinline__ void step_block2(const StepArgs& a, const int tile, c
                 }
             }
             if (f >= z0 + 1 && inT) {
-                Real grad[3][3];
+                Real gn[D];                           // d u_q / d z
 #pragma unroll
-                for (int aa = 0; aa < 3; ++aa)
-#pragma unroll
-                    for (int qq = 0; qq < 3; ++qq) grad[aa][qq] = 0;
-#pragma unroll
-                for (int qq = 0; qq < D; ++qq) grad[V][qq] = (vt1[qq] - vt2[qq]) * kc.invdx[V];
+                for (int q = 0; q < D; ++q) gn[q] = (vt1[q] - vt2[q]) * kc.invdx[V];
+                Real tau[D];
+                Real divu = gn[V];
 #pragma unroll
                 for (int tt = 0; tt < D - 1; ++tt) {
                     const int st = tt == 0 ? SX : SY;
-#pragma unroll
-                    for (int qq = 0; qq < D; ++qq)
-                        grad[tt][qq] = Real(0.25) * (SZ[qq * NT + st] - SZ[qq * NT - st]) * kc.invdx[tt];
+                    tau[tt] = mu * (gn[tt] + (SZ[V * NT + st] - SZ[V * NT - st]) * qt[tt]);
+                    divu += (SZ[tt * NT + st] - SZ[tt * NT - st]) * qt[tt];
                 }
-                Real divu = 0;
-#pragma unroll
-                for (int aa = 0; aa < D; ++aa) divu += grad[aa][aa];
+                tau[V] = mu2 * gn[V] + eta * divu;
                 Real work = 0;
 #pragma unroll
-                for (int qq = 0; qq < D; ++qq) {
-                    Real tau = mu * (grad[V][qq] + grad[qq][V]);
-                    if (qq == V) tau += eta * divu;
-                    work += tau * Real(0.5) * (vt2[qq] + vt1[qq]);
-                    zv_new[qq] = tau;
+                for (int q = 0; q < D; ++q) {
+                    work += tau[q] * (vt2[q] + vt1[q]);
+                    zv_new[q] = tau[q];
                 }
-                zv_new[D] = work + kappa * (vt1[D] - vt2[D]) * kc.invdx[V];
+                zv_new[D] = Real(0.5) * work + (vt1[D] - vt2[D]) * kinv[V];
             }
         }
 
