@@ -59,6 +59,7 @@ ark::StepArgs ark::base_args(const ark_handle* h)
     a.cfl = p.cfl;
     a.low_mach = p.low_mach;
     a.energy_form = p.energy_form;
+    a.work_per_block = h->work_per_block;
     a.planes = h->planes;
     a.tiles_x = h->tiles_x;
     a.tiles_y = h->tiles_y;
@@ -132,6 +133,19 @@ void choose_launch(ark_handle* h, int nsm)
     h->tiles_y = dim == 3 ? (h->p.grid.n[1] + h->kinfo.ty - 1) / h->kinfo.ty : 1;
     const int tiles = h->tiles_x * h->tiles_y;
     const int nv = nv_of(h);
+    if (h->kinfo.balanced) {
+        // one wave of resident blocks; block b takes units [b W, (b + 1) W) of the
+        // tile-major list of (tile, plane) units, as runs of planes per tile.
+        // W >= 16 keeps the pipeline warm-up (4 fronts per run) small.
+        const long long total = (long long)tiles * nv;
+        const long long resident = (long long)nsm * h->kinfo.blocks_per_sm;
+        long long W = (total + resident - 1) / resident;
+        if (W < 16) W = 16;
+        h->work_per_block = W;
+        h->planes = (int)(W < nv ? W : nv);
+        h->grid = dim3((unsigned)((total + W - 1) / W), 1, 1);
+        return;
+    }
     // enough blocks for ~4 waves of resident blocks, each marching >= 8 planes
     const long long want = 4LL * nsm * h->kinfo.blocks_per_sm;
     long long chunks = (want + tiles - 1) / tiles;

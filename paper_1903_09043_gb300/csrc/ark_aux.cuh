@@ -33,6 +33,7 @@ struct StepKernelInfo {
     int tx, ty, threads;
     size_t smem;
     int blocks_per_sm;
+    bool balanced = false;   // grid of resident blocks, each an equal share of (tile, plane) units
 };
 StepKernelInfo step_kernel_2d(int prec, int visc);
 StepKernelInfo step_kernel_3d(int prec, int visc);

@@ -29,6 +29,7 @@ struct ark_handle {
     ark::StepKernelInfo kinfo{};
     dim3 grid;
     int planes = 1, tiles_x = 1, tiles_y = 1;
+    long long work_per_block = 0;  // balanced schedule only
     std::string err;
 };
 

@@ -112,7 +112,8 @@ __device__ __forceinline__ void flux_update_n(float* c, const float* a, float s,
 }
 
 template <int DIM, typename Real, bool SPLIT, bool VISC, int R2X, int R2Y>
-__device__ __forceinline__ void step_block2(const StepArgs& a, const int tile, const int chunk, unsigned char* smem_raw)
+__device__ __forceinline__ void step_block2(const StepArgs& a, const int tile, const int z0, const int z1, const bool lead,
+                                            unsigned char* smem_raw)
 {
     using C = Step2Cfg<DIM, Real, SPLIT, VISC, R2X, R2Y>;
     constexpr int D = DIM, NF = DIM + 2, V = DIM - 1, NT = C::NT, TX = C::TX, TY = C::TY;
@@ -126,8 +127,6 @@ __device__ __forceinline__ void step_block2(const StepArgs& a, const int tile, c
     const int lx = t % R2X - 2, ly = t / R2X - C::HY;
     const int x0 = (tile % a.tiles_x) * TX;
     const int y0 = D == 3 ? (tile / a.tiles_x) * TY : 0;
-    const int z0 = chunk * a.planes;
-    const int z1 = min(z0 + a.planes, S.nv);
     const int nx = S.nx, ny = S.ny, nv = S.nv;
     const long long N = S.N;
 
@@ -146,7 +145,7 @@ __device__ __forceinline__ void step_block2(const StepArgs& a, const int tile, c
     if (t == 0) {
         double dt_d = a.dt_fixed;
         if (!(dt_d > 0.0)) dt_d = a.cfl / __longlong_as_double((long long)a.smax[a.slot_read]);
-        if (tile == 0 && chunk == 0) {
+        if (lead) {   // once per step: clear the slot two steps ahead, advance the clock
             a.smax[a.slot_reset] = 0ull;
             *a.time += dt_d;
             *a.dt_last = dt_d;
@@ -171,8 +170,15 @@ __device__ __forceinline__ void step_block2(const StepArgs& a, const int tile, c
 
     // loader position of this column (clamped into the ghost range); cell
     // offsets within a field are 32-bit (the FP32 forms need ncell < 2^32)
-    const int gx = min(max(x0 + lx, -2), nx + 1);
-    const int gy = D == 3 ? min(max(y0 + ly, -2), ny + 1) : 0;
+    // position of this column; across a periodic in-plane boundary the halo
+    // column is the interior column on the other side (loaded directly, as the
+    // ghost rule would give), otherwise clamped into the ghost range
+    auto wrap = [](int g, int n) { return g < 0 ? g + n : (g >= n ? g - n : g); };   // |g| stays within 2 of the box
+    int gxw = x0 + lx, gyw = D == 3 ? y0 + ly : 0;
+    if (a.bc_lo[0] == BC_PERIODIC && nx >= 2) gxw = wrap(gxw, nx);
+    if (D == 3 && a.bc_lo[1] == BC_PERIODIC && ny >= 2) gyw = wrap(gyw, ny);
+    const int gx = min(max(gxw, -2), nx + 1);
+    const int gy = D == 3 ? min(max(gyw, -2), ny + 1) : 0;
     const bool colin = gx >= 0 && gx < nx && (D == 2 || (gy >= 0 && gy < ny));
     const unsigned plane_cells = D == 3 ? (unsigned)nx * (unsigned)ny : (unsigned)nx;
     const unsigned cidx = D == 3 ? (unsigned)gx + (unsigned)nx * (unsigned)gy : (unsigned)gx;
@@ -600,7 +606,22 @@ template <int DIM, typename Real, bool SPLIT, bool VISC, int R2X, int R2Y>
 __global__ void __launch_bounds__(R2X * R2Y, 512 / (R2X * R2Y)) ark_step2_kernel(const __grid_constant__ StepArgs a)
 {
     extern __shared__ __align__(16) unsigned char smem_raw[];
-    step_block2<DIM, Real, SPLIT, VISC, R2X, R2Y>(a, blockIdx.x, blockIdx.y, smem_raw);
+    // balanced schedule: this block's share of the tile-major (tile, plane) units,
+    // marched as one run of planes per tile it touches
+    const int nv = a.n[DIM - 1];
+    const long long total = (long long)a.tiles_x * a.tiles_y * nv;
+    long long u = (long long)blockIdx.x * a.work_per_block;
+    const long long end = min(u + a.work_per_block, total);
+    bool lead = blockIdx.x == 0;
+    while (u < end) {
+        const int tile = (int)(u / nv);
+        const int z0 = (int)(u - (long long)tile * nv);
+        const int z1 = (int)min((long long)nv, z0 + (end - u));
+        step_block2<DIM, Real, SPLIT, VISC, R2X, R2Y>(a, tile, z0, z1, lead, smem_raw);
+        u += z1 - z0;
+        lead = false;
+        __syncthreads();   // the next run reuses the shared exchange arrays
+    }
 }
 
 template <int DIM, typename Real, bool SPLIT, bool VISC, int R2X, int R2Y>
@@ -618,7 +639,10 @@ ark_batch2_kernel(const StepArgs* __restrict__ runs, const BatchItem* __restrict
         if (it >= nitems) break;
         if (it == 0 && threadIdx.x == 0) ctr[ctr_next] = 0;
         const BatchItem w = items[it];
-        step_block2<DIM, Real, SPLIT, VISC, R2X, R2Y>(runs[w.run], w.tile, w.chunk, smem_raw);
+        const StepArgs& r = runs[w.run];
+        const int z0 = w.chunk * r.planes;
+        step_block2<DIM, Real, SPLIT, VISC, R2X, R2Y>(r, w.tile, z0, min(z0 + r.planes, r.n[DIM - 1]),
+                                                      w.tile == 0 && w.chunk == 0, smem_raw);
     }
 }
 

@@ -35,6 +35,7 @@ StepKernelInfo step2_info()
     k.threads = C::NT;
     k.smem = C::SMEM_BYTES;
     k.blocks_per_sm = 512 / C::NT;
+    k.balanced = true;
     return k;
 }
 
