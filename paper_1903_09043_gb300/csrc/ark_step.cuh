@@ -548,15 +548,20 @@ __device__ __forceinline__ void step_block(const StepArgs& a, const int tile, co
     const bool ocol = ogx < nx && (D == 2 || ogy < ny);
 
     // this thread's load slots (fixed in-plane positions)
+    // (across a periodic in-plane boundary a halo cell is the interior cell on
+    // the other side, loaded directly; walls and outflow take the ghost rule)
     int sgx[NSLOT], sgy[NSLOT];
     bool sin[NSLOT];
     long long sidx[NSLOT];
+    auto wrap = [](int g, int n) { return g < 0 ? g + n : (g >= n ? g - n : g); };
+    const bool perx = a.bc_lo[0] == BC_PERIODIC && nx >= 2, pery = D == 3 && a.bc_lo[1] == BC_PERIODIC && ny >= 2;
 #pragma unroll
     for (int s = 0; s < NSLOT; ++s) {
         const int c = tid + s * NT;
         const int lx = c % C::R2X - 2, ly = c / C::R2X - C::HY;
-        sgx[s] = min(max(x0 + lx, -2), nx + 1);
-        sgy[s] = D == 3 ? min(max(y0 + ly, -2), ny + 1) : 0;
+        const int gxw = perx ? wrap(x0 + lx, nx) : x0 + lx, gyw = pery ? wrap(y0 + ly, ny) : y0 + ly;
+        sgx[s] = min(max(gxw, -2), nx + 1);
+        sgy[s] = D == 3 ? min(max(gyw, -2), ny + 1) : 0;
         sin[s] = c < NR2 && sgx[s] >= 0 && sgx[s] < nx && (D == 2 || (sgy[s] >= 0 && sgy[s] < ny));
         sidx[s] = D == 3 ? sgx[s] + (long long)nx * sgy[s] : sgx[s];
     }
