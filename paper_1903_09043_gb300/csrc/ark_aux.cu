@@ -194,12 +194,17 @@ __global__ void __launch_bounds__(AUX_THREADS) diag_kernel(const StepArgs a, con
 
 __global__ void diag_final_kernel(const double* partials, int nblocks, double* out)
 {
-    // one thread per quantity, blocks in index order: a fixed summation order
+    // the partials are staged in shared memory by the whole block (coalesced),
+    // then one thread per quantity sums them in block index order: a fixed
+    // summation order, without a chain of dependent global loads
+    extern __shared__ double sp[];
+    for (int i = threadIdx.x; i < nblocks * DG_NTOT; i += blockDim.x) sp[i] = partials[i];
+    __syncthreads();
     const int k = threadIdx.x;
     if (k >= DG_NTOT) return;
-    double v = partials[k];
+    double v = sp[k];
     for (int b = 1; b < nblocks; ++b) {
-        const double x = partials[b * DG_NTOT + k];
+        const double x = sp[b * DG_NTOT + k];
         if (k < DG_NSUM || k == DG_NAN) v += x;
         else if (k == DG_UMAX) v = fmax(v, x);
         else v = fmin(v, x);
@@ -288,7 +293,7 @@ cudaError_t launch_diagnostics(const StepArgs& a, int prec, const void* U, doubl
     }
     cudaError_t e = cudaGetLastError();
     if (e != cudaSuccess) return e;
-    diag_final_kernel<<<1, 32, 0, s>>>(partials, g, out);
+    diag_final_kernel<<<1, 256, (size_t)g * DG_NTOT * sizeof(double), s>>>(partials, g, out);
     return cudaGetLastError();
 }
 
