@@ -150,10 +150,14 @@ ark_status ark_destroy(ark_handle* h);
  * (on_device = 0) or on the current device (on_device = 1).  For
  * ARK_F32_SPLIT the FP64 base state is the horizontal mean of rho and p of
  * each row along the gravity axis of U.  Resets t, step and status.  The
- * caller keeps ownership of U; the call returns after U may be reused. */
+ * caller keeps ownership of U; the call returns after U may be reused.
+ * With a host U and an FP32 form, the first call allocates a device staging
+ * buffer of nf * N doubles that h keeps until ark_destroy (ARK_ERR_ALLOC if
+ * it cannot); host transfers run fastest from pinned memory. */
 ark_status ark_set_state(ark_handle* h, const double* U, int on_device);
 
-/* Store the state into U (same layout, FP64), host or device memory. */
+/* Store the state into U (same layout, FP64), host or device memory (a host U
+ * with an FP32 form uses the staging buffer of ark_set_state). */
 ark_status ark_get_state(ark_handle* h, double* U, int on_device);
 
 /* CFL time step of the current state (formula at ark_params.cfl).  Writes it

@@ -125,6 +125,20 @@ ark_status validate(const ark_params* p, std::string& msg)
     return ARK_OK;
 }
 
+// The FP64 staging buffer of host states for the FP32 forms, allocated once
+// per handle on first use (a per-call allocation of this size returns to the
+// OS at the next synchronisation and has to be mapped again every call).
+bool ensure_stage(ark_handle* h, size_t bytes)
+{
+    if (h->stage) return true;
+    if (cudaMalloc((void**)&h->stage, bytes) != cudaSuccess) {
+        cudaGetLastError();
+        h->stage = nullptr;
+        return false;
+    }
+    return true;
+}
+
 void choose_launch(ark_handle* h, int nsm)
 {
     const int dim = h->dim;
@@ -248,6 +262,7 @@ ark_status ark_destroy(ark_handle* h)
     cudaFree(h->ctrl);
     cudaFree(h->base);
     cudaFree(h->base64);
+    cudaFree(h->stage);
     delete h;
     return ARK_OK;
 }
@@ -257,17 +272,13 @@ ark_status ark_set_state(ark_handle* h, const double* U, int on_device)
     if (!h || !U) return fail(h, ARK_ERR_INVALID_ARG, "null argument");
     const size_t bytes64 = (size_t)h->nf * h->N * sizeof(double);
     const double* src = U;
-    double* tmp = nullptr;
     if (!on_device) {
         if (h->prec == ARK_F64) {
             ARK_CUDA(h, cudaMemcpyAsync(h->U[h->cur], U, bytes64, cudaMemcpyHostToDevice, h->stream));
         } else {
-            if (cudaMallocAsync((void**)&tmp, bytes64, h->stream) != cudaSuccess) {
-                cudaGetLastError();
-                return fail(h, ARK_ERR_ALLOC, "staging buffer");
-            }
-            ARK_CUDA(h, cudaMemcpyAsync(tmp, U, bytes64, cudaMemcpyHostToDevice, h->stream));
-            src = tmp;
+            if (!ensure_stage(h, bytes64)) return fail(h, ARK_ERR_ALLOC, "staging buffer");
+            ARK_CUDA(h, cudaMemcpyAsync(h->stage, U, bytes64, cudaMemcpyHostToDevice, h->stream));
+            src = h->stage;
         }
     } else if (h->prec == ARK_F64) {
         ARK_CUDA(h, cudaMemcpyAsync(h->U[h->cur], U, bytes64, cudaMemcpyDeviceToDevice, h->stream));
@@ -283,13 +294,10 @@ ark_status ark_set_state(ark_handle* h, const double* U, int on_device)
         if (e == cudaSuccess) e = cudaMemcpyAsync(hm.data(), means, hm.size() * sizeof(double), cudaMemcpyDeviceToHost, h->stream);
         if (e == cudaSuccess) e = cudaStreamSynchronize(h->stream);
         if (means) cudaFreeAsync(means, h->stream);
-        if (e != cudaSuccess) { if (tmp) cudaFreeAsync(tmp, h->stream); return cuda_fail(h, e, "base state"); }
+        if (e != cudaSuccess) return cuda_fail(h, e, "base state");
         std::vector<double> rho(hm.begin(), hm.begin() + nv), pr(hm.begin() + nv, hm.end());
         for (int r = 0; r < nv; ++r)
-            if (!(rho[r] > 0.0) || !(pr[r] > 0.0)) {
-                if (tmp) cudaFreeAsync(tmp, h->stream);
-                return fail(h, ARK_ERR_NONPHYSICAL, "base state with rho <= 0 or p <= 0");
-            }
+            if (!(rho[r] > 0.0) || !(pr[r] > 0.0)) return fail(h, ARK_ERR_NONPHYSICAL, "base state with rho <= 0 or p <= 0");
         std::vector<double> b64;
         std::vector<float> tab;
         {
@@ -302,14 +310,13 @@ ark_status ark_set_state(ark_handle* h, const double* U, int on_device)
         e = cudaMemcpyAsync(h->base64, b64.data(), b64.size() * sizeof(double), cudaMemcpyHostToDevice, h->stream);
         if (e == cudaSuccess) e = cudaMemcpyAsync(h->base, tab.data(), tab.size() * sizeof(float), cudaMemcpyHostToDevice, h->stream);
         if (e == cudaSuccess) e = cudaStreamSynchronize(h->stream);   // host vectors leave scope
-        if (e != cudaSuccess) { if (tmp) cudaFreeAsync(tmp, h->stream); return cuda_fail(h, e, "base tables"); }
+        if (e != cudaSuccess) return cuda_fail(h, e, "base tables");
         (void)L;
     }
     if (h->prec != ARK_F64) {
         cudaError_t e = ark::launch_convert_in(a, h->prec, src, h->U[h->cur], h->stream);
         if (e != cudaSuccess) st = cuda_fail(h, e, "convert_in");
     }
-    if (tmp) cudaFreeAsync(tmp, h->stream);
     if (st != ARK_OK) return st;
     ARK_CUDA(h, cudaMemsetAsync(h->ctrl, 0, 128, h->stream));   // smax slots, status, time, dt
     h->step = 0;
@@ -330,17 +337,12 @@ ark_status ark_get_state(ark_handle* h, double* U, int on_device)
     } else {
         ark::StepArgs a = base_args(h);
         double* dst = U;
-        double* tmp = nullptr;
         if (!on_device) {
-            if (cudaMallocAsync((void**)&tmp, bytes64, h->stream) != cudaSuccess) {
-                cudaGetLastError();
-                return fail(h, ARK_ERR_ALLOC, "staging buffer");
-            }
-            dst = tmp;
+            if (!ensure_stage(h, bytes64)) return fail(h, ARK_ERR_ALLOC, "staging buffer");
+            dst = h->stage;
         }
         cudaError_t e = ark::launch_convert_out(a, h->prec, h->U[h->cur], dst, h->stream);
-        if (e == cudaSuccess && tmp) e = cudaMemcpyAsync(U, tmp, bytes64, cudaMemcpyDeviceToHost, h->stream);
-        if (tmp) cudaFreeAsync(tmp, h->stream);
+        if (e == cudaSuccess && !on_device) e = cudaMemcpyAsync(U, h->stage, bytes64, cudaMemcpyDeviceToHost, h->stream);
         if (e != cudaSuccess) return cuda_fail(h, e, "get_state");
     }
     if (!on_device) ARK_CUDA(h, cudaStreamSynchronize(h->stream));

@@ -107,12 +107,13 @@ __global__ void __launch_bounds__(AUX_THREADS) row_means_kernel(const StepArgs a
     for (long long i = threadIdx.x; i < plane; i += AUX_THREADS) {
         const long long idx = r * plane + i;
         const double rho = U[idx];
-        double ke = 0.0;
+        double m2 = 0.0;
 #pragma unroll
         for (int d = 0; d < D; ++d) {
             const double m = U[(1 + d) * a.ncell + idx];
-            ke += 0.5 * m * m / rho;
+            m2 += m * m;
         }
+        const double ke = 0.5 * m2 / rho;   // one FP64 division per cell
         accr += rho;
         accp += (a.gamma - 1.0) * (U[(D + 1) * a.ncell + idx] - ke - rho * phi);
     }
