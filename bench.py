@@ -182,24 +182,31 @@ def job_throughput(cells_per_rank, ms_per_step_local, world):
     return cells_per_rank * world / (ms_max * 1e-3), ms_max
 
 
-def cpu_baseline(prob, U, seconds=10.0):
-    """The FP64 oracle on one-step slabs of the workload (8 z planes each)."""
+def cpu_baseline(prob, U, seconds=10.0, single_seconds=4.0):
+    """The FP64 oracle on one-step slabs of the workload (8 z planes each), on
+    all host cores (the reported value) and on one core."""
     import oracle as O
     cores = os.cpu_count() or 1
-    O.set_threads(cores)
     dt = O.dt(prob, U)
     nz = prob.n[2]
-    cells = 0
-    t0 = time.perf_counter()
-    k = 0
-    while time.perf_counter() - t0 < seconds:
-        z0 = (8 * k) % (nz - 8)
-        O.step_window(prob, U, dt, [0, 0, z0], [prob.n[0], prob.n[1], z0 + 8])
-        cells += prob.n[0] * prob.n[1] * 8
-        k += 1
-    el = time.perf_counter() - t0
-    return {"value": cells / el, "unit": UNIT, "cores": cores, "kind": "oracle",
-            "sample": f"{k} one-step slabs of 512x512x8 cells of the workload (FP64 oracle, OpenMP {cores} threads)"}
+
+    def rate(threads, budget):
+        O.set_threads(threads)
+        cells, k = 0, 0
+        t0 = time.perf_counter()
+        while time.perf_counter() - t0 < budget:
+            z0 = (8 * k) % (nz - 8)
+            O.step_window(prob, U, dt, [0, 0, z0], [prob.n[0], prob.n[1], z0 + 8])
+            cells += prob.n[0] * prob.n[1] * 8
+            k += 1
+        return cells / (time.perf_counter() - t0), k
+
+    value, k = rate(cores, seconds)
+    single, k1 = rate(1, single_seconds)
+    return {"value": value, "unit": UNIT, "cores": cores, "kind": "oracle",
+            "sample": f"{k} one-step slabs of 512x512x8 cells of the workload (FP64 oracle, OpenMP {cores} threads)",
+            "single_thread": {"value": single, "unit": UNIT, "cores": 1,
+                              "sample": f"{k1} one-step slabs of 512x512x8 cells, one thread"}}
 
 
 def run_reference(args, world, rank):
@@ -333,12 +340,16 @@ def batch_path(args, stream, hbm):
     for s in solvers:
         s.close()
     achieved = cells * ALG_BYTES[("f32split", 2)] / (ms * 1e-3) / 1e9
+    flops = ALG_FLOPS[(2, all(p.mu > 0 or p.kappa > 0 for p in probs))]
+    tflops = cells * flops / (ms * 1e-3) / 1e12
     return {"value": cells / (ms * 1e-3), "ms_per_step": ms, "runs": len(runs), "cells": cells, "dtype": "f32",
             "one_at_a_time_value": cells / (ms_one * 1e-3), "one_at_a_time_ms_per_step": ms_one,
             "speedup_vs_one_at_a_time": ms_one / ms, "tile": shape, "tuned": {"tx": tx, "planes": planes},
             "launches_per_step": 1, "runs_with_status": bad,
-            "roofline": {"bound": "hbm", "achieved": achieved, "peak": hbm, "unit": "GB/s", "frac": achieved / hbm,
-                         "alg_bytes_per_cell": ALG_BYTES[("f32split", 2)], "traffic": None}}
+            "roofline": {"bound": "alu", "achieved": tflops, "peak": ALU_PEAK_TFLOPS["f32"], "unit": "TFLOP/s",
+                         "frac": tflops / ALU_PEAK_TFLOPS["f32"], "alg_flops_per_cell": flops, "traffic": None,
+                         "hbm": {"achieved": achieved, "peak": hbm, "unit": "GB/s", "frac": achieved / hbm,
+                                 "alg_bytes_per_cell": ALG_BYTES[("f32split", 2)]}}}
 
 
 def main():
