@@ -39,6 +39,7 @@ class _Problem(ctypes.Structure):
         ("T_lo", ctypes.c_double * 3),
         ("T_hi", ctypes.c_double * 3),
         ("energy_form", ctypes.c_int),
+        ("phi", ctypes.POINTER(ctypes.c_double)),
     ]
 
 
@@ -103,6 +104,15 @@ def _struct(prob) -> _Problem:
     s.cfl = float(prob.cfl)
     s.low_mach = int(prob.low_mach)
     s.energy_form = int(getattr(prob, "energy_form", 0))
+    phi = getattr(prob, "phi", None)
+    if phi is not None:
+        arr = np.ascontiguousarray(phi, dtype=np.float64)
+        if arr.shape != tuple(prob.shape):
+            raise ValueError("phi must have the shape of one field")
+        s._phi_keep = arr                      # the array outlives the call through the struct
+        s.phi = arr.ctypes.data_as(ctypes.POINTER(ctypes.c_double))
+    else:
+        s.phi = ctypes.POINTER(ctypes.c_double)()
     return s
 
 

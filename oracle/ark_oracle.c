@@ -72,15 +72,43 @@ static long ncells(const orc_problem* P)
     return (long)P->n[0] * P->n[1] * (P->dim == 3 ? P->n[2] : 1);
 }
 
-/* R11: Phi = -g . x at the centre of cell index ijk (ghosts included). */
+/* Phi at the centre of cell index ijk (ghosts included).
+ * R11: Phi = -g . x for uniform gravity.
+ * R20: a caller-supplied Phi is given at the interior cell centres; a ghost
+ * takes, axis by axis as the state does (the last out-of-range axis first, on
+ * cells that may be ghosts of earlier axes), the value across a periodic
+ * side, or the linear extension of the two nearest interior cells of that
+ * axis across a wall or outflow side: Phi_g = (1 + L) Phi_0 - L Phi_1 for
+ * ghost layer L = 1, 2 (Phi_0 the boundary cell, Phi_1 its inner neighbour). */
 static double phi_at(const orc_problem* P, const int ijk[3])
 {
-    double phi = 0.0;
-    for (int d = 0; d < P->dim; ++d) {
-        double x = P->lo[d] + (ijk[d] + 0.5) * P->dx[d];
-        phi -= P->g[d] * x;
+    if (!P->phi) {
+        double phi = 0.0;
+        for (int d = 0; d < P->dim; ++d) {
+            double x = P->lo[d] + (ijk[d] + 0.5) * P->dx[d];
+            phi -= P->g[d] * x;
+        }
+        return phi;
     }
-    return phi;
+    int d;
+    for (d = P->dim - 1; d >= 0; --d)
+        if (ijk[d] < 0 || ijk[d] >= P->n[d]) break;
+    if (d < 0) {
+        long idx = ijk[0] + (long)P->n[0] * (ijk[1] + (long)P->n[1] * (P->dim == 3 ? ijk[2] : 0));
+        return P->phi[idx];
+    }
+    int n = P->n[d];
+    int lo_side = ijk[d] < 0;
+    int bc = lo_side ? P->bc_lo[d] : P->bc_hi[d];
+    int a[3] = {ijk[0], ijk[1], ijk[2]}, b[3] = {ijk[0], ijk[1], ijk[2]};
+    if (bc == ORC_BC_PERIODIC) {
+        a[d] = ((ijk[d] % n) + n) % n;
+        return phi_at(P, a);
+    }
+    int layer = lo_side ? -ijk[d] : ijk[d] - n + 1;
+    a[d] = lo_side ? 0 : n - 1;
+    b[d] = lo_side ? 1 : n - 2;
+    return (1.0 + layer) * phi_at(P, a) - layer * phi_at(P, b);
 }
 
 /* Primitives from conserved values (Sec. 4 ideal gas, R = 1):

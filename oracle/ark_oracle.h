@@ -30,6 +30,10 @@ typedef struct {
     int energy_form;    /* 0: rho*calE = rho e + rho u^2/2 + rho Phi (Eq. 6, the
                            scheme of Sec. 2); 1: rho E = rho e + rho u^2/2 with
                            the gravity work as a source (Appendix B) */
+    const double* phi;  /* NULL: Phi = -g . x.  Else the potential at the cell
+                           centres, one value per cell in the layout of a field
+                           (R20: ghost values wrap across periodic sides and
+                           extend linearly across walls and outflow) */
 } orc_problem;
 
 int orc_nfields(const orc_problem* P);

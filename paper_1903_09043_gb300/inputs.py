@@ -50,6 +50,8 @@ class Problem:
     T_lo: Tuple[float, float, float] = (0.0, 0.0, 0.0)
     T_hi: Tuple[float, float, float] = (0.0, 0.0, 0.0)
     energy_form: int = 0           # 0: rho*calE with rho*Phi (Sec. 2); 1: rho E, gravity as a source (Appendix B)
+    # caller-supplied potential at the cell centres (shape of one field); None: Phi = -g * x_last
+    phi: np.ndarray | None = dataclasses.field(default=None, compare=False, repr=False)
 
     @property
     def nfields(self) -> int:
@@ -74,6 +76,13 @@ class Problem:
     def centers(self, d: int) -> np.ndarray:
         return self.lo[d] + (np.arange(self.n[d]) + 0.5) * self.dx[d]
 
+    def potential(self) -> np.ndarray:
+        """Phi at every cell centre (shape of one field)."""
+        if self.phi is not None:
+            return np.asarray(self.phi, dtype=np.float64)
+        v = -self.g * self.centers(self.dim - 1)
+        return np.broadcast_to(v.reshape((-1,) + (1,) * (self.dim - 1)), self.shape)
+
     def replace(self, **kw) -> "Problem":
         return dataclasses.replace(self, **kw)
 
@@ -87,7 +96,7 @@ def _assemble(prob: Problem, rho: np.ndarray, vel: Sequence[np.ndarray], p: np.n
     rho = np.broadcast_to(rho, shape).astype(np.float64)
     p = np.broadcast_to(p, shape).astype(np.float64)
     vel = [np.broadcast_to(v, shape).astype(np.float64) for v in vel]
-    phi = -prob.g * _last_axis_centers(prob)
+    phi = prob.potential()
     U = np.empty((prob.nfields,) + shape, dtype=np.float64)
     U[0] = rho
     ke = np.zeros(shape)
@@ -121,7 +130,7 @@ def to_energy_form(prob: Problem, U: np.ndarray, form: int) -> Tuple[Problem, np
     """The same physical state with the energy variable of ``form`` (adds or
     removes rho*Phi; no step arithmetic)."""
     V = np.array(U, dtype=np.float64, copy=True)
-    phi = -prob.g * _last_axis_centers(prob)
+    phi = prob.potential()
     if prob.energy_form == 0 and form == 1:
         V[prob.dim + 1] -= V[0] * phi
     elif prob.energy_form == 1 and form == 0:
@@ -312,6 +321,58 @@ def rayleigh_taylor(n: Sequence[int] = (200, 600), C: float = 0.01, g: float = -
     Lx, Ly = 0.5, 1.5
     v = 0.25 * C * (1.0 + np.cos(2.0 * np.pi * x / Lx)) * (1.0 + np.cos(2.0 * np.pi * y / Ly))
     return prob, _assemble(prob, rho, [np.zeros((ny, nx)), v], p)
+
+
+def tilted_atmosphere(n: Sequence[int] = (24, 20), gx: float = -0.3, gy: float = -1.0, T: float = 1.0,
+                      low_mach: int = 1, gamma: float = 5.0 / 3.0) -> Tuple[Problem, np.ndarray]:
+    """Isothermal atmosphere at rest under gravity (gx, gy) that is not along an
+    axis, given as a potential array Phi = -gx x - gy y, in a box with
+    reflective hydrostatic walls on all sides.  Built as the discrete
+    equilibrium of Eq. 18 along both axes: for T constant the pressure ratio
+    across a face depends only on that face's Phi step, so
+    p_{i,j} = p_{0,0} r_x^i r_y^j with r = (1 - dPhi / (2T)) / (1 + dPhi / (2T))."""
+    nx, ny = int(n[0]), int(n[1])
+    prob = Problem(dim=2, n=(nx, ny, 1), lo=(0.0, 0.0, 0.0), hi=(1.0, 1.0, 1.0), gamma=gamma, low_mach=low_mach,
+                   bc_lo=(REFLECT_HYDRO, REFLECT_HYDRO, PERIODIC), bc_hi=(REFLECT_HYDRO, REFLECT_HYDRO, PERIODIC))
+    x = prob.centers(0)[None, :]
+    y = prob.centers(1)[:, None]
+    phi = -gx * x - gy * y
+    prob = prob.replace(phi=np.ascontiguousarray(phi * np.ones((ny, nx))))
+    p = np.empty((ny, nx))
+    p[0, 0] = 1.0
+    for i in range(1, nx):
+        dphi = prob.phi[0, i] - prob.phi[0, i - 1]
+        p[0, i] = p[0, i - 1] * (1.0 - dphi / (2.0 * T)) / (1.0 + dphi / (2.0 * T))
+    for j in range(1, ny):
+        dphi = prob.phi[j, :] - prob.phi[j - 1, :]
+        p[j, :] = p[j - 1, :] * (1.0 - dphi / (2.0 * T)) / (1.0 + dphi / (2.0 * T))
+    rho = p / T
+    return prob, _assemble(prob, rho, [np.zeros((ny, nx)), np.zeros((ny, nx))], p)
+
+
+def periodic_potential_state(dim: int = 2, n: Sequence[int] = (24, 20), seed: int = 7, amp: float = 0.05,
+                             A: float = 0.3, mu: float = 0.0, kappa: float = 0.0,
+                             low_mach: int = 1) -> Tuple[Problem, np.ndarray]:
+    """Fully periodic box with the potential Phi = A sin(2 pi x) cos(2 pi y)
+    [cos(2 pi z)] given as an array, and a smooth random state (density,
+    velocity, pressure perturbed by sinusoids of random phase)."""
+    nn = tuple(int(v) for v in n) + (1,) * (3 - len(n))
+    prob = Problem(dim=dim, n=nn, lo=(0.0, 0.0, 0.0), hi=(1.0, 1.0, 1.0), mu=mu, kappa=kappa, low_mach=low_mach)
+    rng = np.random.default_rng(seed)
+    grids = np.meshgrid(*[prob.centers(d) for d in reversed(range(dim))], indexing="ij")[::-1]   # x, y[, z]
+    phi = A * np.sin(2 * np.pi * grids[0]) * np.cos(2 * np.pi * grids[1])
+    if dim == 3:
+        phi = phi * np.cos(2 * np.pi * grids[2])
+    prob = prob.replace(phi=np.ascontiguousarray(phi))
+
+    def smooth():
+        ph = rng.uniform(0, 2 * np.pi, size=dim)
+        return np.prod([np.sin(2 * np.pi * grids[d] + ph[d]) for d in range(dim)], axis=0)
+
+    rho = 1.0 + amp * smooth()
+    p = 1.0 + amp * smooth()
+    vel = [amp * smooth() for _ in range(dim)]
+    return prob, _assemble(prob, rho, vel, p)
 
 
 def random_periodic(dim: int = 2, n: Sequence[int] = (24, 20), seed: int = 0, amp: float = 0.1,

@@ -22,7 +22,7 @@ def sound_speed(prob, U):
     dim = prob.dim
     rho = U[0]
     ke = 0.5 * sum(U[1 + d] ** 2 for d in range(dim)) / rho
-    phi = -prob.g * prob.centers(dim - 1).reshape((-1,) + (1,) * (dim - 1))
+    phi = prob.potential()
     if getattr(prob, "energy_form", 0) == 1:
         phi = 0.0 * phi   # rho E holds no potential energy (Appendix B)
     p = (prob.gamma - 1.0) * (U[dim + 1] - ke - rho * phi)

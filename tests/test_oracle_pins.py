@@ -539,3 +539,79 @@ def test_strongly_stratified_polytrope_stays_at_rest():
     V, _ = O.run(prob, U, 300)
     assert O.diagnostics(prob, V)["max_speed"] < 1e-10
 
+
+
+# --------------------------------------------------------------------------
+# Caller-supplied potential Phi at the cell centres (R20)
+# --------------------------------------------------------------------------
+@pytest.mark.parametrize("low_mach", [1, 0])
+def test_tilted_gravity_atmosphere_is_a_discrete_equilibrium(low_mach):
+    """Gravity not along an axis (a Phi array with steps in x and y, walls on
+    all sides): the isothermal state built by Eq. 18 along both axes stays at
+    rest -- the source S of the in-plane faces balances their pressure jumps."""
+    prob, U = I.tilted_atmosphere((24, 20), gx=-0.3, gy=-1.0, low_mach=low_mach)
+    V, _ = O.run(prob, U, 500)
+    assert O.diagnostics(prob, V)["max_speed"] < 1e-12
+
+
+def test_potential_array_equal_to_uniform_gravity_gives_the_same_steps():
+    """Phi given as an array equal to -g y reproduces the uniform-gravity steps
+    (to rounding: the wall ghosts of the array extend Phi linearly instead of
+    evaluating -g y)."""
+    prob, U = I.stratified_random(2, (12, 16), mu=0.01, kappa=0.02)
+    probA = prob.replace(phi=np.ascontiguousarray(np.array(prob.potential())), g=0.0)
+    A, _ = O.run(prob, U, 30)
+    B, _ = O.run(probA, U, 30)
+    assert np.max(np.abs(A - B)) <= 1e-13 * np.max(np.abs(A))
+
+
+def test_gravity_along_x_is_the_transposed_gravity_along_y():
+    """Gravity along x through a Phi array, walls in x, equals the transposed
+    run of the built-in gravity along y: pins S, the momentum source and the
+    hydrostatic wall ghosts on in-plane faces against the gravity axis."""
+    prob, U = I.stratified_random(2, (10, 14), mu=0.01, kappa=0.02)
+    n = 20
+    V, _ = O.run(prob, U, n)
+    probT = I.Problem(dim=2, n=(14, 10, 1), lo=(0.0, 0.0, 0.0), hi=(prob.hi[1], prob.hi[0], 1.0), gamma=prob.gamma,
+                      mu=prob.mu, kappa=prob.kappa, low_mach=prob.low_mach,
+                      bc_lo=(prob.bc_lo[1], prob.bc_lo[0], I.PERIODIC), bc_hi=(prob.bc_hi[1], prob.bc_hi[0], I.PERIODIC),
+                      T_lo=(prob.T_lo[1], prob.T_lo[0], 0.0), T_hi=(prob.T_hi[1], prob.T_hi[0], 0.0),
+                      phi=np.ascontiguousarray(np.array(prob.potential()).T))
+    UT = np.stack([U[0].T, U[2].T, U[1].T, U[3].T])
+    VT, _ = O.run(probT, UT, n)
+    back = np.stack([VT[0].T, VT[2].T, VT[1].T, VT[3].T])
+    assert np.max(np.abs(back - V)) <= 1e-13 * np.max(np.abs(V))
+
+
+def test_periodic_potential_conserves_mass_and_energy():
+    """Time-independent Phi in a periodic box: mass and rho*calE telescope
+    exactly (Sec. 2.1); the momentum changes (the potential exerts a force)."""
+    prob, U = I.periodic_potential_state(2, (24, 20), A=0.3)
+    d0 = O.diagnostics(prob, U)
+    V, _ = O.run(prob, U, 200)
+    d1 = O.diagnostics(prob, V)
+    assert d1["mass"] == pytest.approx(d0["mass"], rel=1e-13)
+    assert d1["energy"] == pytest.approx(d0["energy"], rel=1e-13)
+    assert abs(d1["mom_x"] - d0["mom_x"]) > 1e-6
+
+
+def test_ghost_potential_extends_a_linear_potential_exactly():
+    """R20 on a linear Phi: the ghost values of both layers, at sides, edges
+    and corners, across walls and outflow, are the values of the same linear
+    function at the ghost centres (and wrap across periodic sides)."""
+    g = (-0.7, -1.3)
+    prob = I.Problem(dim=2, n=(6, 5, 1), lo=(0.0, 0.0, 0.0), hi=(1.2, 0.5, 1.0),
+                     bc_lo=(I.OUTFLOW, I.REFLECT_HYDRO, I.PERIODIC), bc_hi=(I.REFLECT_HYDRO, I.OUTFLOW, I.PERIODIC))
+    xs = lambda d, i: prob.lo[d] + (i + 0.5) * prob.dx[d]
+    lin = lambda i, j: -g[0] * xs(0, i) - g[1] * xs(1, j)
+    phi = np.array([[lin(i, j) for i in range(6)] for j in range(5)])
+    probA = prob.replace(phi=phi)
+    U = I._assemble(probA, np.ones((5, 6)), [np.zeros((5, 6))] * 2, np.ones((5, 6)))
+    for i in range(-2, 8):
+        for j in range(-2, 7):
+            c = O.cell_at(probA, U, (i, j, 0))
+            assert c["phi"] == pytest.approx(lin(i, j), rel=0, abs=1e-14), (i, j)
+    # periodic side: the value wraps
+    probP = probA.replace(bc_lo=(I.PERIODIC, I.REFLECT_HYDRO, I.PERIODIC), bc_hi=(I.PERIODIC, I.OUTFLOW, I.PERIODIC))
+    assert O.cell_at(probP, U, (-1, 2, 0))["phi"] == phi[2, 5]
+    assert O.cell_at(probP, U, (7, 1, 0))["phi"] == phi[1, 1]
