@@ -85,6 +85,14 @@ typedef struct {
     double g;                  /* uniform gravity along the LAST axis (y in 2D, z in
                                   3D): Phi = -g * x_last at cell centres; g < 0 pulls
                                   toward the low side.  Phi is time independent.       */
+    const double* phi;         /* NULL, or a host array of N values: the potential at
+                                  the cell centres (layout of one field), any
+                                  direction; then g must be 0.  ark_create copies it.
+                                  Ghost values wrap across periodic sides and extend
+                                  linearly from the two nearest interior cells across
+                                  walls and outflow.  The gravity source S then acts
+                                  on every face (Sec. 2.1.2).  Supported by ARK_F32;
+                                  other precisions return ARK_ERR_UNSUPPORTED.        */
 } ark_gravity;
 
 typedef struct {

@@ -52,7 +52,7 @@ class ark_eos(ctypes.Structure):
 
 
 class ark_gravity(ctypes.Structure):
-    _fields_ = [("g", ctypes.c_double)]
+    _fields_ = [("g", ctypes.c_double), ("phi", ctypes.POINTER(ctypes.c_double))]
 
 
 class ark_bc(ctypes.Structure):
@@ -154,6 +154,12 @@ def params_from_problem(prob, precision: int = ARK_F64) -> ark_params:
         p.bc.T_hi[d] = float(prob.T_hi[d])
     p.eos.gamma = float(prob.gamma)
     p.gravity.g = float(prob.g)
+    phi = getattr(prob, "phi", None)
+    if phi is not None:   # caller-supplied potential: a host array ark_create copies
+        arr = np.ascontiguousarray(phi, dtype=np.float64)
+        p._phi_keep = arr
+        p.gravity.phi = arr.ctypes.data_as(ctypes.POINTER(ctypes.c_double))
+        p.gravity.g = 0.0
     p.mu = float(prob.mu)
     p.kappa = float(prob.kappa)
     p.low_mach = int(prob.low_mach)

@@ -60,6 +60,7 @@ ark::StepArgs ark::base_args(const ark_handle* h)
     a.low_mach = p.low_mach;
     a.energy_form = p.energy_form;
     a.work_per_block = h->work_per_block;
+    a.phiA = h->phiA;
     a.planes = h->planes;
     a.tiles_x = h->tiles_x;
     a.tiles_y = h->tiles_y;
@@ -103,6 +104,13 @@ ark_status validate(const ark_params* p, std::string& msg)
     if (p->bc.lo[dim - 1] == ARK_BC_PERIODIC && p->gravity.g != 0.0) {
         msg = "gravity along a periodic axis"; return ARK_ERR_INVALID_ARG;
     }
+    if (p->gravity.phi) {
+        if (p->gravity.g != 0.0) { msg = "gravity.g must be 0 when gravity.phi is given"; return ARK_ERR_INVALID_ARG; }
+        if (p->precision != ARK_F32) {
+            msg = "a potential array is supported by ARK_F32 (the split form's base state needs Phi = Phi(row))";
+            return ARK_ERR_UNSUPPORTED;
+        }
+    }
     if (!(p->eos.gamma > 1.0)) { msg = "eos.gamma must be > 1"; return ARK_ERR_INVALID_ARG; }
     if (!(p->K >= 1.0)) { msg = "K must be >= 1 (sub-characteristic condition)"; return ARK_ERR_INVALID_ARG; }
     if (!(p->cfl > 0.0)) { msg = "cfl must be > 0"; return ARK_ERR_INVALID_ARG; }
@@ -142,7 +150,8 @@ bool ensure_stage(ark_handle* h, size_t bytes)
 void choose_launch(ark_handle* h, int nsm)
 {
     const int dim = h->dim;
-    h->kinfo = dim == 2 ? ark::step_kernel_2d(h->prec, h->visc) : ark::step_kernel_3d(h->prec, h->visc);
+    h->kinfo = h->phiA ? ark::step_kernel_phi(dim, h->prec, h->visc)
+                       : (dim == 2 ? ark::step_kernel_2d(h->prec, h->visc) : ark::step_kernel_3d(h->prec, h->visc));
     h->tiles_x = (h->p.grid.n[0] + h->kinfo.tx - 1) / h->kinfo.tx;
     h->tiles_y = dim == 3 ? (h->p.grid.n[1] + h->kinfo.ty - 1) / h->kinfo.ty : 1;
     const int tiles = h->tiles_x * h->tiles_y;
@@ -239,6 +248,23 @@ ark_status ark_create(const ark_params* p, void* cuda_stream, ark_handle** out)
         ark_destroy(h);
         return ARK_ERR_ALLOC;
     }
+    if (p->gravity.phi) {   // the caller's potential, in the state precision, owned by the handle
+        std::vector<float> f32;
+        const void* src = p->gravity.phi;
+        if (h->esz == 4) {
+            f32.resize((size_t)h->N);
+            for (long long i = 0; i < h->N; ++i) f32[i] = (float)p->gravity.phi[i];
+            src = f32.data();
+        }
+        if (cudaMalloc(&h->phiA, (size_t)h->N * h->esz) != cudaSuccess) {
+            cudaGetLastError();
+            ark_destroy(h);
+            return ARK_ERR_ALLOC;
+        }
+        e = cudaMemcpy(h->phiA, src, (size_t)h->N * h->esz, cudaMemcpyHostToDevice);
+        if (e != cudaSuccess) { st = cuda_fail(h, e, "potential upload"); ark_destroy(h); return st; }
+        h->p.gravity.phi = nullptr;   // the caller's array is not referenced after ark_create
+    }
     char* c = (char*)h->ctrl;
     h->smax = (unsigned long long*)c;              // 3 slots
     h->status = (unsigned int*)(c + 32);
@@ -263,6 +289,7 @@ ark_status ark_destroy(ark_handle* h)
     cudaFree(h->base);
     cudaFree(h->base64);
     cudaFree(h->stage);
+    cudaFree(h->phiA);
     delete h;
     return ARK_OK;
 }

@@ -45,7 +45,8 @@ __global__ void __launch_bounds__(AUX_THREADS) wave_rate_kernel(const __grid_con
         Real b[D + 2];
 #pragma unroll
         for (int k = 0; k < D + 2; ++k) b[k] = __ldg(U + k * a.ncell + idx);
-        const Row<Real> w = row_info<Real, SPLIT>(a, ph, row_of(a, idx), nv);
+        Row<Real> w = row_info<Real, SPLIT>(a, ph, row_of(a, idx), nv);
+        if (a.phiA && !a.energy_form) w.phi = __ldg(static_cast<const Real*>(a.phiA) + idx);   // caller's Phi
         Real p, rho;
         const Real sh = wave_rate<D, Real, SPLIT, VISC>(b, w, gm1, gamma, invdx, mu, kappa, p, rho);
         if (!(sh <= smax)) smax = (sh == sh) ? sh : smax;
@@ -149,7 +150,8 @@ __global__ void __launch_bounds__(AUX_THREADS) diag_kernel(const StepArgs a, con
     for (long long idx = blockIdx.x * (long long)blockDim.x + threadIdx.x; idx < a.ncell;
          idx += (long long)gridDim.x * blockDim.x) {
         const int r = row_of(a, idx);
-        const double phi = a.energy_form ? 0.0 : -(a.g * (a.lo_v + (r + 0.5) * a.dx[D - 1]));
+        double phi = a.energy_form ? 0.0 : -(a.g * (a.lo_v + (r + 0.5) * a.dx[D - 1]));
+        if (a.phiA && !a.energy_form) phi = double(static_cast<const Real*>(a.phiA)[idx]);   // caller's Phi
         double rho = double(U[idx]), W = double(U[(D + 1) * a.ncell + idx]);
         if constexpr (SPLIT) {
             rho += a.base64[0 * (nv + 4) + r + 2];

@@ -37,6 +37,7 @@ struct StepKernelInfo {
 };
 StepKernelInfo step_kernel_2d(int prec, int visc);
 StepKernelInfo step_kernel_3d(int prec, int visc);
+StepKernelInfo step_kernel_phi(int dim, int prec, int visc);   // caller-supplied potential array
 
 // Batched 2D step-kernel instances (ark_batch_2d*.cu): tile widths 64, 128, 256.
 struct BatchKernelInfo {

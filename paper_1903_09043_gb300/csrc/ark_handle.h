@@ -17,6 +17,7 @@ struct ark_handle {
     void* base = nullptr;          // Real table [nv + 4][BSTRIDE], row-major
     double* base64 = nullptr;      // FP64 rho0, p0, W0 [3][nv + 4]
     double* stage = nullptr;       // FP64 staging of host states (FP32 forms), nf * N, made on first use
+    void* phiA = nullptr;          // caller-supplied potential, N values of the state precision
     void* ctrl = nullptr;          // smax[3] | status | pad | time | dt_last | diag out[16] | partials
     unsigned long long* smax = nullptr;
     unsigned int* status = nullptr;

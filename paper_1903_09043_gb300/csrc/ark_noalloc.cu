@@ -102,6 +102,7 @@ extern "C" ark_status ark_compute_dt_noalloc(const ark_params* p, const double* 
     const int dim = p->grid.dim;
     if (dim != 2 && dim != 3) return ARK_ERR_INVALID_ARG;
     if (p->precision != ARK_F64) return ARK_ERR_INVALID_ARG;
+    if (p->gravity.phi) return ARK_ERR_UNSUPPORTED;   // the potential array would need a device copy
     if (!(p->eos.gamma > 1.0) || !(p->cfl > 0.0) || !(p->mu >= 0.0) || !(p->kappa >= 0.0)) return ARK_ERR_INVALID_ARG;
     long long ncell = 1;
     ark::StepArgs a;

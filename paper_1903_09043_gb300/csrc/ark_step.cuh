@@ -326,7 +326,40 @@ __device__ __forceinline__ Real wave_rate(const Real* b, const Row<Real>& w, Rea
     return sh;
 }
 
-template <int DIM, typename Real, bool SPLIT, bool VISC, int TX, int TY>
+// Potential of a caller-supplied array at any cell within two layers of the
+// box (R20): interior cells read the array; a ghost resolves its out-of-range
+// axes from the last to the first, as the state's ghost rule does -- across a
+// periodic side it takes the cell on the other side, across a wall or outflow
+// side the linear extension (1 + L) Phi_0 - L Phi_1 of the boundary cell and
+// its inner neighbour along that axis (ghost layer L = 1, 2).
+template <int AX, typename Real>
+__device__ Real phi_resolve(const StepArgs& a, const Real* __restrict__ P, int i0, int i1, int i2)
+{
+    if constexpr (AX < 0) {
+        return __ldg(P + (i0 + (long long)a.n[0] * (i1 + (long long)a.n[1] * i2)));
+    } else {
+        int idx[3] = {i0, i1, i2};
+        const int n = a.n[AX];
+        if (idx[AX] >= 0 && idx[AX] < n) return phi_resolve<AX - 1, Real>(a, P, i0, i1, i2);
+        const bool lo = idx[AX] < 0;
+        const int bc = lo ? a.bc_lo[AX] : a.bc_hi[AX];
+        if (bc == BC_PERIODIC) {
+            idx[AX] = ((idx[AX] % n) + n) % n;
+            return phi_resolve<AX - 1, Real>(a, P, idx[0], idx[1], idx[2]);
+        }
+        const int layer = lo ? -idx[AX] : idx[AX] - n + 1;
+        int jdx[3] = {i0, i1, i2};
+        idx[AX] = lo ? 0 : n - 1;
+        jdx[AX] = lo ? 1 : n - 2;
+        return Real(1 + layer) * phi_resolve<AX - 1, Real>(a, P, idx[0], idx[1], idx[2]) -
+               Real(layer) * phi_resolve<AX - 1, Real>(a, P, jdx[0], jdx[1], jdx[2]);
+    }
+}
+
+// Loader of any cell within two layers of the tile, boundary rules included.
+// PHIA: the potential is the caller's array (phi_resolve) instead of -g x_last,
+// so ghosts across in-plane walls see its jumps too.
+template <int DIM, typename Real, bool SPLIT, bool VISC, int TX, int TY, bool PHIA = false>
 struct Stepper {
     using C = StepCfg<DIM, Real, SPLIT, VISC, TX, TY>;
     static constexpr int D = DIM;
@@ -352,6 +385,27 @@ struct Stepper {
         gm1 = kc.gm1;
     }
 
+    // Phi at (gx, gy, gv) (ghosts included), in the state precision
+    __device__ Real phi_cell(int gx, int gy, int gv) const
+    {
+        if constexpr (PHIA) {
+            const Real* P = static_cast<const Real*>(a.phiA);
+            return D == 3 ? phi_resolve<2, Real>(a, P, gx, gy, gv) : phi_resolve<1, Real>(a, P, gx, gv, 0);
+        } else {
+            return phi(gv);
+        }
+    }
+    // the row values of plane gv with the potential of cell (gx, gy, gv)
+    __device__ Row<Real> at(const Row<Real>& w, int gx, int gy, int gv) const
+    {
+        if constexpr (PHIA) {
+            Row<Real> r = w;
+            r.phi = a.energy_form ? Real(0) : phi_cell(gx, gy, gv);
+            return r;
+        } else {
+            return w;
+        }
+    }
     __device__ Cell<D, Real> load_in(int gx, int gy, int gv, const Row<Real>& w) const
     {
         long long idx = D == 3 ? gx + (long long)nx * (gy + (long long)ny * gv) : gx + (long long)nx * gv;
@@ -360,26 +414,35 @@ struct Stepper {
 #pragma unroll
         for (int d = 0; d < D; ++d) c.m[d] = __ldg(U + (1 + d) * N + idx);
         c.dW = __ldg(U + (D + 1) * N + idx);
-        prim<D, Real, SPLIT>(c, w, gm1, gamma);
+        prim<D, Real, SPLIT>(c, at(w, gx, gy, gv), gm1, gamma);
         return c;
     }
 
     // in-plane axis rule (axis 0 = x, axis 1 = y in 3D).  All in-plane
-    // ghosts share the row of their plane; dPhi = 0 across in-plane walls.
+    // ghosts share the row of their plane; for uniform gravity along the last
+    // axis dPhi = 0 across in-plane walls, with a Phi array the wall ghost sees
+    // the array's jump (ghost minus inner neighbour).
     __device__ Cell<D, Real> fetch_x(int gx, int gy, int gv, const Row<Real>& w) const
     {
         if (gx >= 0 && gx < nx) return load_in(gx, gy, gv, w);
         const bool lo = gx < 0;
         const int bc = lo ? a.bc_lo[0] : a.bc_hi[0];
         if (bc == BC_PERIODIC) return load_in(((gx % nx) + nx) % nx, gy, gv, w);
-        if (bc == BC_OUTFLOW) return load_in(lo ? 0 : nx - 1, gy, gv, w);
+        if (bc == BC_OUTFLOW) {
+            Cell<D, Real> M = load_in(lo ? 0 : nx - 1, gy, gv, w);
+            if constexpr (PHIA) cons_from_prim<D, Real, SPLIT>(M, at(w, gx, gy, gv), gm1, gamma);
+            return M;
+        }
         const Real Tw = Real(lo ? a.Tw_lo[0] : a.Tw_hi[0]);
-        const Cell<D, Real> M0 = load_in(lo ? 0 : nx - 1, gy, gv, w);
-        Cell<D, Real> g1 = wall_ghost<D, Real, SPLIT>(M0, M0, bc, 0, Tw, w, Real(0), gm1, gamma);
+        const int x0 = lo ? 0 : nx - 1, x1 = lo ? 1 : nx - 2, g1 = lo ? -1 : nx;
+        const Cell<D, Real> M0 = load_in(x0, gy, gv, w);
+        const Real d1 = PHIA ? phi_cell(g1, gy, gv) - phi_cell(x0, gy, gv) : Real(0);
+        Cell<D, Real> g1c = wall_ghost<D, Real, SPLIT>(M0, M0, bc, 0, Tw, at(w, g1, gy, gv), d1, gm1, gamma);
         const int layer = lo ? -gx : gx - nx + 1;
-        if (layer == 1) return g1;
-        const Cell<D, Real> M1 = load_in(lo ? 1 : nx - 2, gy, gv, w);
-        return wall_ghost<D, Real, SPLIT>(M1, g1, bc, 0, Tw, w, Real(0), gm1, gamma);
+        if (layer == 1) return g1c;
+        const Cell<D, Real> M1 = load_in(x1, gy, gv, w);
+        const Real d2 = PHIA ? phi_cell(gx, gy, gv) - phi_cell(g1, gy, gv) : Real(0);
+        return wall_ghost<D, Real, SPLIT>(M1, g1c, bc, 0, Tw, at(w, gx, gy, gv), d2, gm1, gamma);
     }
 
     __device__ Cell<D, Real> fetch_h(int gx, int gy, int gv, const Row<Real>& w) const
@@ -389,14 +452,21 @@ struct Stepper {
                 const bool lo = gy < 0;
                 const int bc = lo ? a.bc_lo[1] : a.bc_hi[1];
                 if (bc == BC_PERIODIC) return fetch_x(gx, ((gy % ny) + ny) % ny, gv, w);
-                if (bc == BC_OUTFLOW) return fetch_x(gx, lo ? 0 : ny - 1, gv, w);
+                if (bc == BC_OUTFLOW) {
+                    Cell<D, Real> M = fetch_x(gx, lo ? 0 : ny - 1, gv, w);
+                    if constexpr (PHIA) cons_from_prim<D, Real, SPLIT>(M, at(w, gx, gy, gv), gm1, gamma);
+                    return M;
+                }
                 const Real Tw = Real(lo ? a.Tw_lo[1] : a.Tw_hi[1]);
-                const Cell<D, Real> M0 = fetch_x(gx, lo ? 0 : ny - 1, gv, w);
-                Cell<D, Real> g1 = wall_ghost<D, Real, SPLIT>(M0, M0, bc, 1, Tw, w, Real(0), gm1, gamma);
+                const int y0 = lo ? 0 : ny - 1, y1 = lo ? 1 : ny - 2, g1 = lo ? -1 : ny;
+                const Cell<D, Real> M0 = fetch_x(gx, y0, gv, w);
+                const Real d1 = PHIA ? phi_cell(gx, g1, gv) - phi_cell(gx, y0, gv) : Real(0);
+                Cell<D, Real> g1c = wall_ghost<D, Real, SPLIT>(M0, M0, bc, 1, Tw, at(w, gx, g1, gv), d1, gm1, gamma);
                 const int layer = lo ? -gy : gy - ny + 1;
-                if (layer == 1) return g1;
-                const Cell<D, Real> M1 = fetch_x(gx, lo ? 1 : ny - 2, gv, w);
-                return wall_ghost<D, Real, SPLIT>(M1, g1, bc, 1, Tw, w, Real(0), gm1, gamma);
+                if (layer == 1) return g1c;
+                const Cell<D, Real> M1 = fetch_x(gx, y1, gv, w);
+                const Real d2 = PHIA ? phi_cell(gx, gy, gv) - phi_cell(gx, g1, gv) : Real(0);
+                return wall_ghost<D, Real, SPLIT>(M1, g1c, bc, 1, Tw, at(w, gx, gy, gv), d2, gm1, gamma);
             }
         }
         return fetch_x(gx, gy, gv, w);
@@ -418,7 +488,7 @@ struct Stepper {
             const int s = lo ? 0 : nv - 1;
             Cell<D, Real> M = fetch_h(gx, gy, s, row_info<Real, SPLIT>(a, phi, s, nv));
             Cell<D, Real> g = M;   // (rho, u, p) copied; base rows of an outflow ghost copy the edge row
-            cons_from_prim<D, Real, SPLIT>(g, wg, gm1, gamma);
+            cons_from_prim<D, Real, SPLIT>(g, at(wg, gx, gy, gv), gm1, gamma);
             return g;
         }
         const Real Tw = Real(lo ? a.Tw_lo[V] : a.Tw_hi[V]);
@@ -426,13 +496,13 @@ struct Stepper {
         const Row<Real> w0 = row_info<Real, SPLIT>(a, phi, r0, nv);
         const Row<Real> w1g = row_info<Real, SPLIT>(a, phi, g1r, nv);
         const Cell<D, Real> M0 = fetch_h(gx, gy, r0, w0);
-        const Real dphi1 = phi(g1r) - phi(r0);
-        Cell<D, Real> g1 = wall_ghost<D, Real, SPLIT>(M0, M0, bc, V, Tw, w1g, dphi1, gm1, gamma);
+        const Real dphi1 = phi_cell(gx, gy, g1r) - phi_cell(gx, gy, r0);
+        Cell<D, Real> g1 = wall_ghost<D, Real, SPLIT>(M0, M0, bc, V, Tw, at(w1g, gx, gy, g1r), dphi1, gm1, gamma);
         if (gv == g1r) return g1;
         const Row<Real> w1 = row_info<Real, SPLIT>(a, phi, r1, nv);
         const Cell<D, Real> M1 = fetch_h(gx, gy, r1, w1);
-        const Real dphi2 = phi(gv) - phi(g1r);
-        return wall_ghost<D, Real, SPLIT>(M1, g1, bc, V, Tw, wg, dphi2, gm1, gamma);
+        const Real dphi2 = phi_cell(gx, gy, gv) - phi_cell(gx, gy, g1r);
+        return wall_ghost<D, Real, SPLIT>(M1, g1, bc, V, Tw, at(wg, gx, gy, gv), dphi2, gm1, gamma);
     }
 };
 

@@ -31,20 +31,24 @@
 
 namespace ark {
 
-template <int DIM, typename Real, bool SPLIT, bool VISC, int R2X_, int R2Y_>
+template <int DIM, typename Real, bool SPLIT, bool VISC, int R2X_, int R2Y_, bool PHIA = false>
 struct Step2Cfg {
     static constexpr int D = DIM, NF = DIM + 2, V = DIM - 1;
     static constexpr int R2X = R2X_, R2Y = R2Y_, NT = R2X * R2Y;
     static constexpr int HY = DIM == 3 ? 2 : 0, H1 = DIM == 3 ? 1 : 0;
     static constexpr int TX = R2X - 4, TY = DIM == 3 ? R2Y - 4 : 1;
-    static constexpr int NPX = DIM == 3 ? 6 : 5;                  // in-plane face inputs: u_x[, u_y], dp, z, rz, rc
+    // in-plane face inputs: u_x[, u_y], dp, z, rz, rc (+ rho, Phi with a potential array)
+    static constexpr int XI_DP = DIM - 1, XI_Z = XI_DP + 1, XI_RZ = XI_DP + 2, XI_RC = XI_DP + 3;
+    static constexpr int XI_RHO = XI_DP + 4, XI_PHI = XI_DP + 5;
+    static constexpr int NPX = XI_RC + 1 + (PHIA ? 2 : 0);
+    static constexpr int NFF = PHIA ? 3 : 2;                      // per in-plane face: u*, dPi* (+ S)
     static constexpr int NVT = DIM + (VISC ? 1 : 0);              // velocity (+ temperature)
     static constexpr int NV = DIM + 1;                            // dissipative flux components
     static constexpr int NDIR = DIM - 1;                          // in-plane directions
     // shared memory, in units of Real, each array indexed by thread
     static constexpr int O_X = 0;                                 // [NPX]       plane f primitives
-    static constexpr int O_FF = O_X + NPX * NT;                   // [NDIR][2]   u*, dPi* of own in-plane faces
-    static constexpr int O_TL = O_FF + NDIR * 2 * NT;             // [NF]        tilde state
+    static constexpr int O_FF = O_X + NPX * NT;                   // [NDIR][NFF] u*, dPi* (, S) of own in-plane faces
+    static constexpr int O_TL = O_FF + NDIR * NFF * NT;           // [NF]        tilde state
     static constexpr int O_TF = O_TL + NF * NT;                   // [NDIR][NF]  upwind transport fluxes
     static constexpr int O_VT = O_TF + NDIR * NF * NT;            // [NVT]       velocity, T (VISC)
     static constexpr int O_DZ = O_VT + (VISC ? NVT * NT : 0);     // [D]         vertical velocity difference (VISC)
@@ -56,6 +60,7 @@ struct Step2Cfg {
     static constexpr size_t O_RED = O_BASE + (SPLIT ? BRING * BSTRIDE * sizeof(float) : 0);
     static constexpr size_t SMEM_BYTES = O_RED + NT * sizeof(double) + 4 * sizeof(double);
     static_assert(NT % 32 == 0 && NT <= 1024, "block must be whole warps");
+    static_assert(!(PHIA && SPLIT), "the split form's base state needs Phi = Phi(row)");
 };
 
 // Four consecutive base-table entries of one row.  The block keeps the rows
@@ -111,18 +116,19 @@ __device__ __forceinline__ void flux_update_n(float* c, const float* a, float s,
     }
 }
 
-template <int DIM, typename Real, bool SPLIT, bool VISC, int R2X, int R2Y>
+template <int DIM, typename Real, bool SPLIT, bool VISC, int R2X, int R2Y, bool PHIA = false>
 __device__ __forceinline__ void step_block2(const StepArgs& a, const int tile, const int z0, const int z1, const bool lead,
                                             unsigned char* smem_raw)
 {
-    using C = Step2Cfg<DIM, Real, SPLIT, VISC, R2X, R2Y>;
+    using C = Step2Cfg<DIM, Real, SPLIT, VISC, R2X, R2Y, PHIA>;
     constexpr int D = DIM, NF = DIM + 2, V = DIM - 1, NT = C::NT, TX = C::TX, TY = C::TY;
     static_assert(!SPLIT || sizeof(Real) == 4, "the split form stores FP32 deviations");
     Real* sm = reinterpret_cast<Real*>(smem_raw);
     double* red = reinterpret_cast<double*>(smem_raw + C::O_RED);
     float* const bring = reinterpret_cast<float*>(smem_raw + C::O_BASE);
 
-    const Stepper<DIM, Real, SPLIT, VISC, C::TX, C::TY> S(a);
+    const Stepper<DIM, Real, SPLIT, VISC, C::TX, C::TY, PHIA> S(a);
+    constexpr int NFF = C::NFF;
     const int t = threadIdx.x;
     const int lx = t % R2X - 2, ly = t / R2X - C::HY;
     const int x0 = (tile % a.tiles_x) * TX;
@@ -188,11 +194,14 @@ __device__ __forceinline__ void step_block2(const StepArgs& a, const int tile, c
     Real* __restrict__ Uo = static_cast<Real*>(a.Uout);
 
     Real raw[NF];
+    Real rawphi = 0;                  // potential of the prefetched cell (PHIA)
+    const Real* __restrict__ Pa = static_cast<const Real*>(a.phiA);
     auto prefetch = [&](int p) {
         if (colin && p >= 0 && p < nv) {
             const unsigned idx = cidx + plane_cells * (unsigned)p;
 #pragma unroll
             for (int k = 0; k < NF; ++k) raw[k] = __ldg(Uin + k * N + idx);
+            if constexpr (PHIA) rawphi = __ldg(Pa + idx);
         }
     };
     prefetch(z0 - 2);
@@ -210,12 +219,13 @@ __device__ __forceinline__ void step_block2(const StepArgs& a, const int tile, c
 
     // own-column registers
     struct Prev {                     // plane f-1: conserved values and face inputs
-        Real drho, m[D], dW, dp, z, rz, rc;
+        Real drho, m[D], dW, dp, z, rz, rc, phi;
     } cp;
-    cp.drho = cp.dW = cp.dp = cp.z = cp.rz = cp.rc = 0;
+    cp.drho = cp.dW = cp.dp = cp.z = cp.rz = cp.rc = cp.phi = 0;
+    Real phi2 = 0;                    // potential of plane f-2 (PHIA)
 #pragma unroll
     for (int d = 0; d < D; ++d) cp.m[d] = 0;
-    Real fxp[2] = {0, 0}, fyp[2] = {0, 0};   // own +x / +y faces of plane f-1 (u*, dPi*)
+    Real fxp[3] = {0, 0, 0}, fyp[3] = {0, 0, 0};   // own +x / +y faces of plane f-1 (u*, dPi*, S)
     Real fx2 = 0, fy2 = 0;            // u* of the own +x / +y faces of plane f-2
     Real zfl[3] = {0, 0, 0};          // face (f-2, f-1): u*, dPi*, dS
     Real tlA[NF + 1];                 // tilde state (+ L) of plane f-2
@@ -260,6 +270,7 @@ __device__ __forceinline__ void step_block2(const StepArgs& a, const int tile, c
         // ================= H1 =================
         // own cell of plane f
         Cell<D, Real> cc;
+        Real ccphi = 0;               // potential of the own cell (PHIA)
         {
             const bool fin = f >= 0 && f < nv;
             if (fin && colin) {
@@ -267,7 +278,8 @@ __device__ __forceinline__ void step_block2(const StepArgs& a, const int tile, c
                 w.rho0 = SPLIT ? bf0.x : Real(0);
                 w.p0 = SPLIT ? bf0.y : Real(0);
                 w.T0 = SPLIT ? bf0.z : Real(0);
-                w.phi = a.energy_form ? Real(0) : S.phi.at(fr);
+                if constexpr (PHIA) ccphi = rawphi;
+                w.phi = a.energy_form ? Real(0) : (PHIA ? ccphi : S.phi.at(fr));
                 cc.drho = raw[0];
 #pragma unroll
                 for (int d = 0; d < D; ++d) cc.m[d] = raw[1 + d];
@@ -275,6 +287,7 @@ __device__ __forceinline__ void step_block2(const StepArgs& a, const int tile, c
                 prim<D, Real, SPLIT>(cc, w, S.gm1, S.gamma);
             } else {
                 cc = S.fetch(gx, gy, f);
+                if constexpr (PHIA) ccphi = S.phi_cell(gx, gy, f);
             }
         }
         prefetch(f + 1);
@@ -282,10 +295,14 @@ __device__ __forceinline__ void step_block2(const StepArgs& a, const int tile, c
         const Real zc = cc.rho * cc.c, rzc = rcc * cc.rr;
         X[0 * NT] = cc.u[0];
         if constexpr (D == 3) X[1 * NT] = cc.u[1];
-        X[(C::NPX - 4) * NT] = cc.dp;
-        X[(C::NPX - 3) * NT] = zc;
-        X[(C::NPX - 2) * NT] = rzc;
-        X[(C::NPX - 1) * NT] = rcc;
+        X[C::XI_DP * NT] = cc.dp;
+        X[C::XI_Z * NT] = zc;
+        X[C::XI_RZ * NT] = rzc;
+        X[C::XI_RC * NT] = rcc;
+        if constexpr (PHIA) {
+            X[C::XI_RHO * NT] = cc.rho;
+            X[C::XI_PHI * NT] = ccphi;
+        }
         Real vt0[C::NVT];
 #pragma unroll
         for (int d = 0; d < D; ++d) vt0[d] = cc.u[d];
@@ -295,7 +312,7 @@ __device__ __forceinline__ void step_block2(const StepArgs& a, const int tile, c
         Real zfu[3] = {0, 0, 0};
         if (f >= z0 - 1 && inR1) {
             // Phi jump across the face: -g dz for uniform g, rounded once from FP64
-            zfu[2] = Real(-0.5) * (cp.drho + cc.drho) * Real(a.fdphi);
+            zfu[2] = Real(-0.5) * (cp.drho + cc.drho) * (PHIA ? ccphi - cp.phi : Real(a.fdphi));
             acoustic_face<Real>(vt1[V], cc.u[V], cp.dp, cc.dp, cp.z, zc, cp.rz, rzc, cp.rc, rcc,
                                 SPLIT ? Real(b11.x) : Real(0), zfu[2], kc.K, kc.halfInvK, a.low_mach, zfu[0], zfu[1]);
         }
@@ -311,11 +328,21 @@ __device__ __forceinline__ void step_block2(const StepArgs& a, const int tile, c
             Real m_t[D];
             m_t[0] = cp.m[0] - lam[0] * (fxp[1] - pix_m);
             Real W_t = cp.dW - lam[0] * (fxp[1] * fxp[0] - pix_m * usx_m);
+            if constexpr (PHIA) {   // gravity source of the in-plane faces (the caller's Phi varies in x)
+                const Real sx_m = FF[2 * NT - SX];
+                m_t[0] += lam[0] * Real(0.5) * (fxp[2] + sx_m);
+                if (a.energy_form) W_t += lam[0] * Real(0.5) * (fxp[0] * fxp[2] + usx_m * sx_m);
+            }
             if constexpr (D == 3) {
-                const Real usy_m = FF[2 * NT - SY], piy_m = FF[3 * NT - SY];
+                const Real usy_m = FF[NFF * NT - SY], piy_m = FF[(NFF + 1) * NT - SY];
                 ell += lam[1] * (fyp[0] - usy_m);
                 m_t[1] = cp.m[1] - lam[1] * (fyp[1] - piy_m);
                 W_t -= lam[1] * (fyp[1] * fyp[0] - piy_m * usy_m);
+                if constexpr (PHIA) {
+                    const Real sy_m = FF[(NFF + 2) * NT - SY];
+                    m_t[1] += lam[1] * Real(0.5) * (fyp[2] + sy_m);
+                    if (a.energy_form) W_t += lam[1] * Real(0.5) * (fyp[0] * fyp[2] + usy_m * sy_m);
+                }
             }
             ell += lam[V] * (zfu[0] - zfl[0]);
             m_t[V] = cp.m[V] - lam[V] * (zfu[1] - zfl[1]) + lam[V] * Real(0.5) * (zfu[2] + zfl[2]);
@@ -470,22 +497,29 @@ __device__ __forceinline__ void step_block2(const StepArgs& a, const int tile, c
             if (t < BSTRIDE && f + 1 <= nv + 1) bnext = __ldg(Bt + base_index(t, f + 1));
         }
         // own +x / +y acoustic faces of plane f
-        Real fxc[2] = {0, 0}, fyc[2] = {0, 0};
+        Real fxc[3] = {0, 0, 0}, fyc[3] = {0, 0, 0};
         if (f >= z0 - 1 && f <= z1) {
             if (xfR1) {
-                acoustic_face<Real>(cc.u[0], X[SX], cc.dp, X[(C::NPX - 4) * NT + SX], zc, X[(C::NPX - 3) * NT + SX],
-                                    rzc, X[(C::NPX - 2) * NT + SX], rcc, X[(C::NPX - 1) * NT + SX], Real(0), Real(0),
+                // with a Phi array the in-plane faces carry S = -(rho_L + rho_R)(Phi_R - Phi_L) / 2
+                if constexpr (PHIA)
+                    fxc[2] = Real(-0.5) * (cc.rho + X[C::XI_RHO * NT + SX]) * (X[C::XI_PHI * NT + SX] - ccphi);
+                acoustic_face<Real>(cc.u[0], X[SX], cc.dp, X[C::XI_DP * NT + SX], zc, X[C::XI_Z * NT + SX],
+                                    rzc, X[C::XI_RZ * NT + SX], rcc, X[C::XI_RC * NT + SX], Real(0), fxc[2],
                                     kc.K, kc.halfInvK, a.low_mach, fxc[0], fxc[1]);
                 FF[0 * NT] = fxc[0];
                 FF[1 * NT] = fxc[1];
+                if constexpr (PHIA) FF[2 * NT] = fxc[2];
             }
             if constexpr (D == 3) {
                 if (yfR1) {
-                    acoustic_face<Real>(cc.u[1], X[NT + SY], cc.dp, X[2 * NT + SY], zc, X[3 * NT + SY], rzc,
-                                        X[4 * NT + SY], rcc, X[5 * NT + SY], Real(0), Real(0), kc.K, kc.halfInvK,
-                                        a.low_mach, fyc[0], fyc[1]);
-                    FF[2 * NT] = fyc[0];
-                    FF[3 * NT] = fyc[1];
+                    if constexpr (PHIA)
+                        fyc[2] = Real(-0.5) * (cc.rho + X[C::XI_RHO * NT + SY]) * (X[C::XI_PHI * NT + SY] - ccphi);
+                    acoustic_face<Real>(cc.u[1], X[NT + SY], cc.dp, X[C::XI_DP * NT + SY], zc, X[C::XI_Z * NT + SY], rzc,
+                                        X[C::XI_RZ * NT + SY], rcc, X[C::XI_RC * NT + SY], Real(0), fyc[2], kc.K,
+                                        kc.halfInvK, a.low_mach, fyc[0], fyc[1]);
+                    FF[NFF * NT] = fyc[0];
+                    FF[(NFF + 1) * NT] = fyc[1];
+                    if constexpr (PHIA) FF[(NFF + 2) * NT] = fyc[2];
                 }
             }
         }
@@ -545,7 +579,7 @@ __device__ __forceinline__ void step_block2(const StepArgs& a, const int tile, c
                 w.rho0 = SPLIT ? Real(b20.x) : Real(0);
                 w.p0 = SPLIT ? Real(b20.y) : Real(0);
                 w.T0 = SPLIT ? Real(b20.z) : Real(0);
-                w.phi = a.energy_form ? Real(0) : S.phi.at(fr - Real(2));
+                w.phi = a.energy_form ? Real(0) : (PHIA ? phi2 : S.phi.at(fr - Real(2)));
                 Real p, rho;
                 const Real sh = wave_rate<D, Real, SPLIT, VISC>(nb, w, S.gm1, S.gamma, kc.invdx, kc.mu, kc.kappa, p, rho);
                 if (!(sh <= smax_t)) smax_t = (sh == sh) ? sh : smax_t;
@@ -570,10 +604,11 @@ __device__ __forceinline__ void step_block2(const StepArgs& a, const int tile, c
         for (int k = 0; k <= NF; ++k) tlA[k] = tlB[k];
         fx2 = fxp[0];
         fy2 = fyp[0];
-        fxp[0] = fxc[0];
-        fxp[1] = fxc[1];
-        fyp[0] = fyc[0];
-        fyp[1] = fyc[1];
+#pragma unroll
+        for (int k = 0; k < 3; ++k) {
+            fxp[k] = fxc[k];
+            fyp[k] = fyc[k];
+        }
 #pragma unroll
         for (int k = 0; k < 3; ++k) zfl[k] = zfu[k];
 #pragma unroll
@@ -589,6 +624,10 @@ __device__ __forceinline__ void step_block2(const StepArgs& a, const int tile, c
         cp.z = zc;
         cp.rz = rzc;
         cp.rc = rcc;
+        if constexpr (PHIA) {
+            phi2 = cp.phi;
+            cp.phi = ccphi;
+        }
     }
 
     // block max of the wave rate -> one atomic per block
@@ -602,7 +641,7 @@ __device__ __forceinline__ void step_block2(const StepArgs& a, const int tile, c
     if (status) atomicOr(a.status, status);
 }
 
-template <int DIM, typename Real, bool SPLIT, bool VISC, int R2X, int R2Y>
+template <int DIM, typename Real, bool SPLIT, bool VISC, int R2X, int R2Y, bool PHIA = false>
 __global__ void __launch_bounds__(R2X * R2Y, 512 / (R2X * R2Y)) ark_step2_kernel(const __grid_constant__ StepArgs a)
 {
     extern __shared__ __align__(16) unsigned char smem_raw[];
@@ -617,7 +656,7 @@ __global__ void __launch_bounds__(R2X * R2Y, 512 / (R2X * R2Y)) ark_step2_kernel
         const int tile = (int)(u / nv);
         const int z0 = (int)(u - (long long)tile * nv);
         const int z1 = (int)min((long long)nv, z0 + (end - u));
-        step_block2<DIM, Real, SPLIT, VISC, R2X, R2Y>(a, tile, z0, z1, lead, smem_raw);
+        step_block2<DIM, Real, SPLIT, VISC, R2X, R2Y, PHIA>(a, tile, z0, z1, lead, smem_raw);
         u += z1 - z0;
         lead = false;
         __syncthreads();   // the next run reuses the shared exchange arrays

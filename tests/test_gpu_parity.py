@@ -380,3 +380,48 @@ def test_bounded_wait_times_out_then_recovers():
         assert ei.value.status == ark.ARK_ERR_TIMEOUT
         s.sync(120.0)
         assert s.diagnostics()["step"] == 20
+
+
+def _x_gravity_case():
+    """Gravity along x through a potential array, walls in x: the transpose of
+    a stratified state under the built-in gravity along y."""
+    prob0, U0 = I.stratified_random(2, (14, 10), mu=0.01, kappa=0.02)
+    probT = I.Problem(dim=2, n=(10, 14, 1), lo=(0.0, 0.0, 0.0), hi=(prob0.hi[1], prob0.hi[0], 1.0), gamma=prob0.gamma,
+                      mu=prob0.mu, kappa=prob0.kappa, low_mach=prob0.low_mach,
+                      bc_lo=(prob0.bc_lo[1], prob0.bc_lo[0], I.PERIODIC),
+                      bc_hi=(prob0.bc_hi[1], prob0.bc_hi[0], I.PERIODIC),
+                      T_lo=(prob0.T_lo[1], prob0.T_lo[0], 0.0), T_hi=(prob0.T_hi[1], prob0.T_hi[0], 0.0),
+                      phi=np.ascontiguousarray(np.array(prob0.potential()).T))
+    return probT, np.stack([U0[0].T, U0[2].T, U0[1].T, U0[3].T])
+
+
+POTENTIAL_CASES = {
+    "2d_tilted_atmosphere": lambda: I.tilted_atmosphere((24, 20)),
+    "2d_periodic_potential_visc": lambda: I.periodic_potential_state(2, (40, 24), mu=0.01, kappa=0.01),
+    "2d_periodic_potential_two_tiles": lambda: I.periodic_potential_state(2, (300, 6)),
+    "3d_periodic_potential_multi_tile": lambda: I.periodic_potential_state(3, (35, 33, 9), mu=0.01, kappa=0.01),
+    "2d_gravity_along_x_walls": _x_gravity_case,
+}
+
+
+@pytest.mark.parametrize("case", sorted(POTENTIAL_CASES))
+def test_potential_array_fp32_matches_oracle(case):
+    """Caller-supplied Phi (R20): the gravity source on every face, the
+    potential read per cell, ghost potentials across walls."""
+    prob, U = POTENTIAL_CASES[case]()
+    n = 20
+    ref, _, dts = O.run(prob, U, n, return_dt=True)
+    V, d = gpu_run(prob, U, n, precision="f32")
+    errs = field_errors(prob, V, ref)
+    assert max(errs) <= n * F32_STEP_TOL, errs
+    assert d["status"] == 0
+    assert d["dt"] == pytest.approx(dts[-1], rel=1e-5)
+
+
+@pytest.mark.parametrize("precision", ["f32split"])
+def test_potential_array_unsupported_precisions(precision):
+    ark = _ark()
+    prob, _ = I.tilted_atmosphere((16, 12))
+    with pytest.raises(ark.ArkError) as ei:
+        ark.Solver(prob, precision, stream=_stream())
+    assert ei.value.status == ark.ARK_ERR_UNSUPPORTED
