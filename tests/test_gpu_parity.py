@@ -392,7 +392,7 @@ def _x_gravity_case():
                       bc_hi=(prob0.bc_hi[1], prob0.bc_hi[0], I.PERIODIC),
                       T_lo=(prob0.T_lo[1], prob0.T_lo[0], 0.0), T_hi=(prob0.T_hi[1], prob0.T_hi[0], 0.0),
                       phi=np.ascontiguousarray(np.array(prob0.potential()).T))
-    return probT, np.stack([U0[0].T, U0[2].T, U0[1].T, U0[3].T])
+    return probT, np.ascontiguousarray(np.stack([U0[0].T, U0[2].T, U0[1].T, U0[3].T]))
 
 
 POTENTIAL_CASES = {
