@@ -91,8 +91,8 @@ typedef struct {
                                   Ghost values wrap across periodic sides and extend
                                   linearly from the two nearest interior cells across
                                   walls and outflow.  The gravity source S then acts
-                                  on every face (Sec. 2.1.2).  Supported by ARK_F32;
-                                  other precisions return ARK_ERR_UNSUPPORTED.        */
+                                  on every face (Sec. 2.1.2).  ARK_F64 and ARK_F32;
+                                  ARK_F32_SPLIT returns ARK_ERR_UNSUPPORTED.          */
 } ark_gravity;
 
 typedef struct {

@@ -106,8 +106,8 @@ ark_status validate(const ark_params* p, std::string& msg)
     }
     if (p->gravity.phi) {
         if (p->gravity.g != 0.0) { msg = "gravity.g must be 0 when gravity.phi is given"; return ARK_ERR_INVALID_ARG; }
-        if (p->precision != ARK_F32) {
-            msg = "a potential array is supported by ARK_F32 (the split form's base state needs Phi = Phi(row))";
+        if (p->precision == ARK_F32_SPLIT) {
+            msg = "a potential array needs ARK_F64 or ARK_F32 (the split form's base state needs Phi = Phi(row))";
             return ARK_ERR_UNSUPPORTED;
         }
     }

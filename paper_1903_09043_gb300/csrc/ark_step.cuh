@@ -31,7 +31,7 @@
 
 namespace ark {
 
-template <int DIM, typename Real, bool SPLIT, bool VISC, int TX, int TY>
+template <int DIM, typename Real, bool SPLIT, bool VISC, int TX, int TY, bool PHIA = false>
 struct StepCfg {
     static constexpr int D = DIM;
     static constexpr int NF = DIM + 2;
@@ -56,11 +56,13 @@ struct StepCfg {
     static constexpr int O_FACEF = O_VELT + 3 * NVT * NR2;             // [2][4][NR2] dp, rc, z, rz
     static constexpr int O_UCONS = O_FACEF + 2 * 4 * NR2;              // [2][NF][NR1]
     static constexpr int O_ZF = O_UCONS + 2 * NF * NR1;                // [2][3][NR1] u*, dPi*, dS
-    static constexpr int O_XYF = O_ZF + 2 * 3 * NR1;                   // [2][2][NFX + NFY]
-    static constexpr int O_TL = O_XYF + 2 * 2 * (NFX + NFY);           // [2][NF + 1][NR1]
+    static constexpr int NXYC = PHIA ? 3 : 2;                          // in-plane face values: u*, dPi* (, S)
+    static constexpr int O_XYF = O_ZF + 2 * 3 * NR1;                   // [2][NXYC][NFX + NFY]
+    static constexpr int O_TL = O_XYF + 2 * NXYC * (NFX + NFY);        // [2][NF + 1][NR1]
     static constexpr int O_TFLUX = O_TL + 2 * (NF + 1) * NR1;          // [NF][NTX + NTY]
     static constexpr int O_VFLUX = O_TFLUX + NF * (NTX + NTY);         // [NV][NTX + NTY]
-    static constexpr int N_REAL = O_VFLUX + (VISC ? NV * (NTX + NTY) : 0);
+    static constexpr int O_PH = O_VFLUX + (VISC ? NV * (NTX + NTY) : 0);   // [2][2][NR2] rho, Phi (PHIA)
+    static constexpr int N_REAL = O_PH + (PHIA ? 2 * 2 * NR2 : 0);
     static constexpr size_t SMEM_BYTES = ((N_REAL * sizeof(Real) + 15) / 16) * 16 + NT * sizeof(double) + 4 * sizeof(double);
 
     static constexpr int TXV = TX, TYV = TY;
@@ -552,30 +554,35 @@ __device__ __forceinline__ void store_cell(const Cell<D, Real>& x, Real* vT, Rea
 
 // Cells of ghost planes and of tiles that touch the box edge: boundary rules,
 // out of line so that the interior path stays in registers.
-template <int DIM, typename Real, bool SPLIT, bool VISC, int TX, int TY>
-__device__ __noinline__ void slow_cell(const Stepper<DIM, Real, SPLIT, VISC, TX, TY> S, int gx, int gy, int f,
-                                       Real* vT, Real* ff, Real* uc, int c, int lx, int ly)
+// PHIA: the cell's density and potential also go to the ring ph (rho, Phi).
+template <int DIM, typename Real, bool SPLIT, bool VISC, int TX, int TY, bool PHIA = false>
+__device__ __noinline__ void slow_cell(const Stepper<DIM, Real, SPLIT, VISC, TX, TY, PHIA> S, int gx, int gy, int f,
+                                       Real* vT, Real* ff, Real* uc, Real* ph, int c, int lx, int ly)
 {
-    using C = StepCfg<DIM, Real, SPLIT, VISC, TX, TY>;
+    using C = StepCfg<DIM, Real, SPLIT, VISC, TX, TY, PHIA>;
     const Cell<DIM, Real> x = S.fetch(gx, gy, f);
     store_cell<C, DIM, Real>(x, vT, ff, uc, c, lx, ly);
+    if constexpr (PHIA) {
+        ph[c] = x.rho;
+        ph[C::NR2 + c] = S.phi_cell(gx, gy, f);
+    }
 }
 
 // One block's share of a step: in-plane tile `tile`, planes [chunk * planes,
 // (chunk + 1) * planes) of the gravity axis.  Called by the single-grid kernel
 // (one block per (tile, chunk)) and by the batched kernel (work items of many runs).
-template <int DIM, typename Real, bool SPLIT, bool VISC, int TX, int TY>
+template <int DIM, typename Real, bool SPLIT, bool VISC, int TX, int TY, bool PHIA = false>
 __device__ __forceinline__ void step_block(const StepArgs& a, const int tile, const int chunk,
                                            unsigned char* smem_raw)
 {
-    using C = StepCfg<DIM, Real, SPLIT, VISC, TX, TY>;
+    using C = StepCfg<DIM, Real, SPLIT, VISC, TX, TY, PHIA>;
     constexpr int D = DIM, NF = DIM + 2, V = DIM - 1;
     constexpr int NT = C::NT, NR1 = C::NR1, NR2 = C::NR2, NVT = C::NVT;
     constexpr int NSLOT = (NR2 + NT - 1) / NT;
     Real* sm = reinterpret_cast<Real*>(smem_raw);
     double* red = reinterpret_cast<double*>(smem_raw + ((C::N_REAL * sizeof(Real) + 15) / 16) * 16);
 
-    const Stepper<DIM, Real, SPLIT, VISC, TX, TY> S(a);
+    const Stepper<DIM, Real, SPLIT, VISC, TX, TY, PHIA> S(a);
     const int tid = threadIdx.x;
     const int x0 = (tile % a.tiles_x) * TX;
     const int y0 = D == 3 ? (tile / a.tiles_x) * TY : 0;
@@ -637,6 +644,8 @@ __device__ __forceinline__ void step_block(const StepArgs& a, const int tile, co
     }
     const long long plane_cells = D == 3 ? (long long)nx * ny : (long long)nx;
     Real raw[NSLOT][NF];
+    Real rawphi[NSLOT];        // caller's potential of the prefetched cells (PHIA)
+    const Real* __restrict__ Pa = static_cast<const Real*>(a.phiA);
     auto prefetch = [&](int p) {
         if (p < 0 || p >= nv) return;
 #pragma unroll
@@ -645,6 +654,7 @@ __device__ __forceinline__ void step_block(const StepArgs& a, const int tile, co
                 const long long idx = sidx[s] + plane_cells * p;
 #pragma unroll
                 for (int k = 0; k < NF; ++k) raw[s][k] = __ldg(U + k * N + idx);
+                if constexpr (PHIA) rawphi[s] = __ldg(Pa + idx);
             }
         }
     };
@@ -673,8 +683,10 @@ __device__ __forceinline__ void step_block(const StepArgs& a, const int tile, co
         Real* const uc_f1 = sm + C::O_UCONS + ((f - 1) & 1) * NF * NR1;
         Real* const zf_up = sm + C::O_ZF + (f & 1) * 3 * NR1;          // face (f-1, f)
         Real* const zf_lo = sm + C::O_ZF + ((f - 1) & 1) * 3 * NR1;    // face (f-2, f-1)
-        Real* const xy_f1 = sm + C::O_XYF + ((f - 1) & 1) * 2 * (C::NFX + C::NFY);
-        Real* const xy_f2 = sm + C::O_XYF + ((f - 2) & 1) * 2 * (C::NFX + C::NFY);
+        Real* const xy_f1 = sm + C::O_XYF + ((f - 1) & 1) * C::NXYC * (C::NFX + C::NFY);
+        Real* const xy_f2 = sm + C::O_XYF + ((f - 2) & 1) * C::NXYC * (C::NFX + C::NFY);
+        Real* const ph_f = sm + C::O_PH + (f & 1) * 2 * NR2;           // rho, Phi of plane f (PHIA)
+        Real* const ph_f1 = sm + C::O_PH + ((f - 1) & 1) * 2 * NR2;    // of plane f-1
         Real* const tl_f1 = sm + C::O_TL + ((f - 1) & 1) * (NF + 1) * NR1;
         Real* const tl_f2 = sm + C::O_TL + ((f - 2) & 1) * (NF + 1) * NR1;
         Real* const tfx = sm + C::O_TFLUX;
@@ -697,10 +709,16 @@ __device__ __forceinline__ void step_block(const StepArgs& a, const int tile, co
 #pragma unroll
                     for (int d = 0; d < D; ++d) x.m[d] = raw[s][1 + d];
                     x.dW = raw[s][D + 1];
-                    prim<D, Real, SPLIT>(x, wf, S.gm1, S.gamma);
+                    Row<Real> w = wf;
+                    if constexpr (PHIA) w.phi = a.energy_form ? Real(0) : rawphi[s];
+                    prim<D, Real, SPLIT>(x, w, S.gm1, S.gamma);
                     store_cell<C, D, Real>(x, vT_f, ff_f, uc_f, c, lx, ly);
+                    if constexpr (PHIA) {
+                        ph_f[c] = x.rho;
+                        ph_f[NR2 + c] = rawphi[s];
+                    }
                 } else {
-                    slow_cell<DIM, Real, SPLIT, VISC, TX, TY>(S, sgx[s], sgy[s], f, vT_f, ff_f, uc_f, c, lx, ly);
+                    slow_cell<DIM, Real, SPLIT, VISC, TX, TY, PHIA>(S, sgx[s], sgy[s], f, vT_f, ff_f, uc_f, ph_f, c, lx, ly);
                 }
             }
         }
@@ -713,24 +731,28 @@ __device__ __forceinline__ void step_block(const StepArgs& a, const int tile, co
             for (int e = tid; e < C::NFX; e += NT) {
                 const int lx = e % C::FXX - 2, ly = e / C::FXX - C::H1;
                 const int iL = C::i2(lx, ly), iR = iL + 1;
-                Real us, dPi;
+                Real us, dPi, dS = Real(0);
+                if constexpr (PHIA) dS = Real(-0.5) * (ph_f1[iL] + ph_f1[iR]) * (ph_f1[NR2 + iR] - ph_f1[NR2 + iL]);
                 acoustic_face<Real>(vT_f1[iL], vT_f1[iR], ff_f1[iL], ff_f1[iR], ff_f1[2 * NR2 + iL],
                                     ff_f1[2 * NR2 + iR], ff_f1[3 * NR2 + iL], ff_f1[3 * NR2 + iR], ff_f1[NR2 + iL],
-                                    ff_f1[NR2 + iR], Real(0), Real(0), K, halfInvK, a.low_mach, us, dPi);
+                                    ff_f1[NR2 + iR], Real(0), dS, K, halfInvK, a.low_mach, us, dPi);
                 xy_f1[e] = us;
                 xy_f1[XYS + e] = dPi;
+                if constexpr (PHIA) xy_f1[2 * XYS + e] = dS;
             }
             if constexpr (D == 3) {
                 for (int e = tid; e < C::NFY; e += NT) {
                     const int lx = e % C::R1X - 1, ly = e / C::R1X - 2;
                     const int iL = C::i2(lx, ly), iR = iL + C::R2X;
-                    Real us, dPi;
+                    Real us, dPi, dS = Real(0);
+                    if constexpr (PHIA) dS = Real(-0.5) * (ph_f1[iL] + ph_f1[iR]) * (ph_f1[NR2 + iR] - ph_f1[NR2 + iL]);
                     acoustic_face<Real>(vT_f1[NR2 + iL], vT_f1[NR2 + iR], ff_f1[iL], ff_f1[iR], ff_f1[2 * NR2 + iL],
                                         ff_f1[2 * NR2 + iR], ff_f1[3 * NR2 + iL], ff_f1[3 * NR2 + iR],
-                                        ff_f1[NR2 + iL], ff_f1[NR2 + iR], Real(0), Real(0), K, halfInvK,
+                                        ff_f1[NR2 + iL], ff_f1[NR2 + iR], Real(0), dS, K, halfInvK,
                                         a.low_mach, us, dPi);
                     xy_f1[C::NFX + e] = us;
                     xy_f1[XYS + C::NFX + e] = dPi;
+                    if constexpr (PHIA) xy_f1[2 * XYS + C::NFX + e] = dS;
                 }
             }
         }
@@ -741,7 +763,7 @@ __device__ __forceinline__ void step_block(const StepArgs& a, const int tile, co
             for (int c = tid; c < NR1; c += NT) {
                 const int lx = c % C::R1X - 1, ly = c / C::R1X - C::H1;
                 const int i = C::i2(lx, ly);
-                const Real dS = Real(-0.5) * (uc_f1[c] + uc_f[c]) * dphi;
+                const Real dS = Real(-0.5) * (uc_f1[c] + uc_f[c]) * (PHIA ? ph_f[NR2 + i] - ph_f1[NR2 + i] : dphi);
                 Real us, dPi;
                 acoustic_face<Real>(vT_f1[V * NR2 + i], vT_f[V * NR2 + i], ff_f1[i], ff_f[i], ff_f1[2 * NR2 + i],
                                     ff_f[2 * NR2 + i], ff_f1[3 * NR2 + i], ff_f[3 * NR2 + i], ff_f1[NR2 + i],
@@ -770,6 +792,11 @@ __device__ __forceinline__ void step_block(const StepArgs& a, const int tile, co
                 Real m_t[D];
                 m_t[0] = uc_f1[NR1 + c] - lam[0] * (pix_p - pix_m);
                 Real W_t = uc_f1[(D + 1) * NR1 + c] - lam[0] * (pix_p * usx_p - pix_m * usx_m);
+                if constexpr (PHIA) {   // gravity source of the in-plane faces (the caller's Phi varies in x)
+                    const Real sx_p = xy_f1[2 * XYS + exp_], sx_m = xy_f1[2 * XYS + exm];
+                    m_t[0] += lam[0] * Real(0.5) * (sx_p + sx_m);
+                    if (a.energy_form) W_t += lam[0] * Real(0.5) * (usx_p * sx_p + usx_m * sx_m);
+                }
                 if constexpr (D == 3) {
                     const int eyp = C::NFX + C::ify(lx, ly), eym = eyp - C::R1X;
                     const Real usy_p = xy_f1[eyp], usy_m = xy_f1[eym];
@@ -777,6 +804,11 @@ __device__ __forceinline__ void step_block(const StepArgs& a, const int tile, co
                     ell += lam[1] * (usy_p - usy_m);
                     m_t[1] = uc_f1[2 * NR1 + c] - lam[1] * (piy_p - piy_m);
                     W_t -= lam[1] * (piy_p * usy_p - piy_m * usy_m);
+                    if constexpr (PHIA) {
+                        const Real sy_p = xy_f1[2 * XYS + eyp], sy_m = xy_f1[2 * XYS + eym];
+                        m_t[1] += lam[1] * Real(0.5) * (sy_p + sy_m);
+                        if (a.energy_form) W_t += lam[1] * Real(0.5) * (usy_p * sy_p + usy_m * sy_m);
+                    }
                 }
                 ell += lam[V] * (usz_p - usz_m);
                 m_t[V] = uc_f1[(1 + V) * NR1 + c] - lam[V] * (piz_p - piz_m) + lam[V] * Real(0.5) * (dSz_p + dSz_m);
@@ -988,7 +1020,8 @@ __device__ __forceinline__ void step_block(const StepArgs& a, const int tile, co
 #pragma unroll
                 for (int k = 0; k < NF; ++k) Uo[k * N + idx] = nb[k];
                 // CFL wave rate of U^{n+1} (next step's dt) and physical checks
-                const Row<Real> w = row_info<Real, SPLIT>(a, S.phi, q, nv, fr - Real(2));
+                Row<Real> w = row_info<Real, SPLIT>(a, S.phi, q, nv, fr - Real(2));
+                if constexpr (PHIA) w.phi = a.energy_form ? Real(0) : __ldg(Pa + idx);
                 Real p, rho;
                 const Real sh = wave_rate<D, Real, SPLIT, VISC>(nb, w, S.gm1, S.gamma, invdx, mu, kappa, p, rho);
                 if (!(sh <= smax_t)) smax_t = (sh == sh) ? sh : smax_t;
@@ -1022,12 +1055,12 @@ __device__ __forceinline__ void step_block(const StepArgs& a, const int tile, co
 }
 
 // One launch = one step of one grid: block (x, y) = (in-plane tile, chunk of planes).
-template <int DIM, typename Real, bool SPLIT, bool VISC, int TX, int TY>
+template <int DIM, typename Real, bool SPLIT, bool VISC, int TX, int TY, bool PHIA = false>
 __global__ void __launch_bounds__(TX * TY, sizeof(Real) == 8 ? 1 : 2)
 ark_step_kernel(const __grid_constant__ StepArgs a)
 {
     extern __shared__ __align__(16) unsigned char smem_raw[];
-    step_block<DIM, Real, SPLIT, VISC, TX, TY>(a, blockIdx.x, blockIdx.y, smem_raw);
+    step_block<DIM, Real, SPLIT, VISC, TX, TY, PHIA>(a, blockIdx.x, blockIdx.y, smem_raw);
 }
 
 // Work item of the batched step: one (run, tile, chunk).

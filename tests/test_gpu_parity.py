@@ -405,17 +405,27 @@ POTENTIAL_CASES = {
 
 
 @pytest.mark.parametrize("case", sorted(POTENTIAL_CASES))
-def test_potential_array_fp32_matches_oracle(case):
+@pytest.mark.parametrize("precision", ["f64", "f32"])
+def test_potential_array_matches_oracle(case, precision):
     """Caller-supplied Phi (R20): the gravity source on every face, the
     potential read per cell, ghost potentials across walls."""
     prob, U = POTENTIAL_CASES[case]()
     n = 20
-    ref, _, dts = O.run(prob, U, n, return_dt=True)
-    V, d = gpu_run(prob, U, n, precision="f32")
+    ref, t_ref, dts = O.run(prob, U, n, return_dt=True)
+    V, d = gpu_run(prob, U, n, precision=precision)
     errs = field_errors(prob, V, ref)
-    assert max(errs) <= n * F32_STEP_TOL, errs
+    assert max(errs) <= (F64_TOL if precision == "f64" else n * F32_STEP_TOL), errs
     assert d["status"] == 0
-    assert d["dt"] == pytest.approx(dts[-1], rel=1e-5)
+    assert d["dt"] == pytest.approx(dts[-1], rel=1e-13 if precision == "f64" else 1e-5)
+
+
+def test_tilted_gravity_atmosphere_stays_at_rest_fp64():
+    """Gravity not along an axis (Phi array), walls on all sides: the discrete
+    equilibrium stays at rest for 1000 GPU steps, as in the oracle."""
+    prob, U = I.tilted_atmosphere((64, 48))
+    V, d = gpu_run(prob, U, 1000)
+    assert d["max_speed"] < 1e-12
+    assert d["status"] == 0
 
 
 @pytest.mark.parametrize("precision", ["f32split"])
