@@ -15,16 +15,6 @@ __device__ __forceinline__ int row_of(const StepArgs& a, long long idx)
     return (int)(idx / plane);
 }
 
-template <typename T>
-__device__ __forceinline__ void block_reduce_max(T& v, double* red)
-{
-    red[threadIdx.x] = double(v);
-    __syncthreads();
-    for (int s = AUX_THREADS / 2; s > 0; s >>= 1) {
-        if (threadIdx.x < s) red[threadIdx.x] = fmax(red[threadIdx.x], red[threadIdx.x + s]);
-        __syncthreads();
-    }
-}
 
 // Wave rate of every cell; one atomicMax per block on the FP64 bit pattern
 // (positive doubles order like their bit patterns, so the result does not
@@ -51,8 +41,7 @@ __global__ void __launch_bounds__(AUX_THREADS) wave_rate_kernel(const __grid_con
         const Real sh = wave_rate<D, Real, SPLIT, VISC>(b, w, gm1, gamma, invdx, mu, kappa, p, rho);
         if (!(sh <= smax)) smax = (sh == sh) ? sh : smax;
     }
-    block_reduce_max(smax, red);
-    if (threadIdx.x == 0) atomicMax(slot, (unsigned long long)__double_as_longlong(red[0]));
+    block_rate_max(double(smax), reinterpret_cast<unsigned long long*>(red), slot);
 }
 
 template <int D, typename Real, bool SPLIT>

@@ -531,6 +531,28 @@ struct IC {
     static constexpr int value = N;
 };
 
+// Block maximum of non-negative CFL rates into *slot: warp-shuffle maxima of
+// the FP64 bit patterns (non-negative doubles order like their bit patterns,
+// so the result is exact and independent of the order), one shared slot per
+// warp, then one atomicMax per block.  Every thread of the block calls it.
+__device__ __forceinline__ void block_rate_max(double v, unsigned long long* red, unsigned long long* slot)
+{
+    unsigned long long b = (unsigned long long)__double_as_longlong(v);
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+        const unsigned long long c = __shfl_xor_sync(0xffffffffu, b, o);
+        b = c > b ? c : b;
+    }
+    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+    if (lane == 0) red[w] = b;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        unsigned long long m = red[0];
+        for (int k = 1; k < (int)(blockDim.x >> 5); ++k) m = red[k] > m ? red[k] : m;
+        atomicMax(slot, m);
+    }
+}
+
 // Store one loaded cell (conserved + primitive values) into the plane rings.
 template <class C, int D, typename Real>
 __device__ __forceinline__ void store_cell(const Cell<D, Real>& x, Real* vT, Real* ff, Real* uc, int c, int lx, int ly)
@@ -1044,13 +1066,7 @@ __device__ __forceinline__ void step_block(const StepArgs& a, const int tile, co
     }
 
     // block max of the wave rate -> one atomic per block
-    red[tid] = double(smax_t);
-    __syncthreads();
-    for (int s = NT / 2; s > 0; s >>= 1) {
-        if (tid < s) red[tid] = fmax(red[tid], red[tid + s]);
-        __syncthreads();
-    }
-    if (tid == 0) atomicMax(a.smax + a.slot_write, (unsigned long long)__double_as_longlong(red[0]));
+    block_rate_max(double(smax_t), reinterpret_cast<unsigned long long*>(red), a.smax + a.slot_write);
     if (status) atomicOr(a.status, status);
 }
 

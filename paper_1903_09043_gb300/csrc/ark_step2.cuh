@@ -631,13 +631,7 @@ __device__ __forceinline__ void step_block2(const StepArgs& a, const int tile, c
     }
 
     // block max of the wave rate -> one atomic per block
-    red[t] = double(smax_t);
-    __syncthreads();
-    for (int s = NT / 2; s > 0; s >>= 1) {
-        if (t < s) red[t] = fmax(red[t], red[t + s]);
-        __syncthreads();
-    }
-    if (t == 0) atomicMax(a.smax + a.slot_write, (unsigned long long)__double_as_longlong(red[0]));
+    block_rate_max(double(smax_t), reinterpret_cast<unsigned long long*>(red), a.smax + a.slot_write);
     if (status) atomicOr(a.status, status);
 }
 
