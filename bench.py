@@ -430,6 +430,15 @@ def main():
     if not args.no_batch:
         with torch.cuda.stream(stream):
             line["paths"]["batch"] = batch_path(args, stream, hbm)
+    # speed-ups at the accuracies the tests hold (FP64 within 1e-12 of the oracle,
+    # the FP32 forms within their per-step budget)
+    sp = {}
+    if "f32split" in results and "f64" in results:
+        sp["f32split_vs_f64"] = results["f64"]["ms_per_step"] / results["f32split"]["ms_per_step"]
+    if "batch" in line["paths"]:
+        sp["batch_vs_one_at_a_time"] = line["paths"]["batch"]["speedup_vs_one_at_a_time"]
+    if sp:
+        line["speedups"] = sp
     if rank == 0 and not args.no_e2e:
         with torch.cuda.stream(stream):
             hprec, hkind = PATHS[head]
