@@ -10,7 +10,9 @@
  *   1. ghost cells (Sec. 3.2: ghost zones carry the physical boundary
  *      conditions), materialised as arrays;
  *   2. conservative -> primitive variables (Sec. 3.2 kernel list; ideal gas of
- *      Sec. 4: p = (gamma-1) rho e, c^2 = gamma p / rho, p = rho T);
+ *      Sec. 4: p = (gamma-1) rho e, c^2 = gamma p / rho, p = rho T; with
+ *      p_inf > 0 the stiffened gas of R21, which the scheme admits as Sec. 4
+ *      notes that another equation of state may be used);
  *   3. acoustic step, Sec. 2.1.2: per-face a, S, u*, theta (Eq. 16,
  *      low_mach_correction), Pi*, then per-cell L~ and tilde states;
  *   4. transport step, Sec. 2.1.3: b^{n+1} = b~ - dt/dx [b~ u*] + b~ dt/dx [u*]
@@ -29,7 +31,7 @@
  *   R1 unsplit multi-D; R2 a = K max(rho_L c_L, rho_R c_R); R3 CFL formula;
  *   R4 dissipative fluxes from U^n in the same update; R5 physical heat-flux
  *   sign; R6 viscous stencil; R7 upwind tie u* >= 0 -> left; R10 wall ghosts;
- *   R11 Phi = -g.x at cell centres.
+ *   R11 Phi = -g.x at cell centres; R21 stiffened-gas equation of state.
  *
  * State layout: nf = dim + 2 fields (rho, m_x, m_y[, m_z], rho*calE), each a
  * block of nx*ny*nz doubles, x fastest.  For dim == 2, nz == 1.
@@ -113,7 +115,11 @@ static double phi_at(const orc_problem* P, const int ijk[3])
 
 /* Primitives from conserved values (Sec. 4 ideal gas, R = 1):
  * e = (W - 1/2 rho |u|^2 - rho Phi) / rho, p = (gamma-1) rho e,
- * T = p / rho, c = sqrt(gamma p / rho). */
+ * T = p / rho, c = sqrt(gamma p / rho).
+ * R21 stiffened gas (Harlow and Amsden 1971; temperature as in Le Metayer,
+ * Massoni and Saurel 2004, with (gamma-1) c_v = 1): p = (gamma-1) rho e -
+ * gamma p_inf, T = (p + p_inf) / rho, c = sqrt(gamma (p + p_inf) / rho);
+ * p_inf = 0 is the ideal gas. */
 static void to_primitive(const orc_problem* P, cell_t* c)
 {
     double ke = 0.0;
@@ -122,9 +128,9 @@ static void to_primitive(const orc_problem* P, cell_t* c)
         ke += 0.5 * c->rho * c->u[d] * c->u[d];
     }
     double rho_e = c->W - ke - (P->energy_form == 0 ? c->rho * c->phi : 0.0);
-    c->p = (P->gamma - 1.0) * rho_e;
-    c->T = c->p / c->rho;
-    c->c = sqrt(P->gamma * c->p / c->rho);
+    c->p = (P->gamma - 1.0) * rho_e - P->gamma * P->p_inf;
+    c->T = (c->p + P->p_inf) / c->rho;
+    c->c = sqrt(P->gamma * (c->p + P->p_inf) / c->rho);
 }
 
 /* Conserved values from (rho, u, p, phi). */
@@ -135,9 +141,10 @@ static void to_conserved(const orc_problem* P, cell_t* c)
         c->m[d] = c->rho * c->u[d];
         ke += 0.5 * c->rho * c->u[d] * c->u[d];
     }
-    c->W = c->p / (P->gamma - 1.0) + ke + (P->energy_form == 0 ? c->rho * c->phi : 0.0);
-    c->T = c->p / c->rho;
-    c->c = sqrt(P->gamma * c->p / c->rho);
+    /* rho e = (p + gamma p_inf) / (gamma - 1) (R21) */
+    c->W = (c->p + P->gamma * P->p_inf) / (P->gamma - 1.0) + ke + (P->energy_form == 0 ? c->rho * c->phi : 0.0);
+    c->T = (c->p + P->p_inf) / c->rho;
+    c->c = sqrt(P->gamma * (c->p + P->p_inf) / c->rho);
 }
 
 static void load_interior(const orc_problem* P, const double* U, const int ijk[3], cell_t* c)
@@ -165,9 +172,9 @@ static void load_interior(const orc_problem* P, const double* U, const int ijk[3
  * temperature; fixed-temperature wall sets T_g = 2 T_wall - T_mirror.
  * Pressure: the discrete hydrostatic balance of Eq. 18 (well_balanced_formula)
  * between the ghost and its inner neighbour A (interior cell 0 for layer 1,
- * ghost layer 1 for layer 2), with rho_g = p_g / T_g:
- *   p_g - p_A = -1/2 (rho_A + p_g / T_g) (Phi_g - Phi_A)
- *   => p_g = (p_A - 1/2 rho_A dPhi) / (1 + dPhi / (2 T_g)).
+ * ghost layer 1 for layer 2), with rho_g = (p_g + p_inf) / T_g:
+ *   p_g - p_A = -1/2 (rho_A + (p_g + p_inf) / T_g) (Phi_g - Phi_A)
+ *   => p_g + p_inf = (p_A + p_inf - 1/2 rho_A dPhi) / (1 + dPhi / (2 T_g)).
  * Outflow: zero-gradient copy of (rho, u, p) of the boundary cell.
  */
 static void cell_at(const orc_problem* P, const double* U, const int ijk[3], cell_t* out)
@@ -224,8 +231,9 @@ static void cell_at(const orc_problem* P, const double* U, const int ijk[3], cel
     }
     out->phi = phi_at(P, ijk);
     double dphi = out->phi - A.phi;
-    out->p = (A.p - 0.5 * A.rho * dphi) / (1.0 + dphi / (2.0 * Tg));
-    out->rho = out->p / Tg;
+    double pi_g = (A.p + P->p_inf - 0.5 * A.rho * dphi) / (1.0 + dphi / (2.0 * Tg));
+    out->p = pi_g - P->p_inf;
+    out->rho = pi_g / Tg;
     to_conserved(P, out);
 }
 

@@ -19,7 +19,7 @@ typedef struct {
     int n[3];           /* cells per axis; n[2] ignored when dim == 2        */
     double lo[3];       /* lower corner of the box                           */
     double dx[3];       /* cell sizes                                        */
-    double gamma;       /* ideal-gas adiabatic index                         */
+    double gamma;       /* adiabatic index                                   */
     double g[3];        /* uniform gravity, Phi = -g . x                     */
     double mu, kappa;   /* dynamic viscosity, heat conductivity              */
     double K;           /* a = K max(rho c) at each face                      */
@@ -34,6 +34,9 @@ typedef struct {
                            centres, one value per cell in the layout of a field
                            (R20: ghost values wrap across periodic sides and
                            extend linearly across walls and outflow) */
+    double p_inf;       /* stiffened-gas constant of the equation of state,
+                           p = (gamma-1) rho e - gamma p_inf, T = (p + p_inf)/rho,
+                           c^2 = gamma (p + p_inf)/rho; 0: the ideal gas (R21) */
 } orc_problem;
 
 int orc_nfields(const orc_problem* P);
