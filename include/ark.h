@@ -14,8 +14,11 @@
  *   - first-order viscous and heat-conduction fluxes (Sec. 2.2);
  *   - the CFL time step of the next step, reduced on the device.
  * rho*calE = rho e + rho |u|^2 / 2 + rho Phi is the total energy including the
- * gravitational energy (Eq. 6, conservation_of_energy); the gas is ideal,
- * p = (gamma - 1) rho e, p = rho T (Sec. 4).
+ * gravitational energy (Eq. 6, conservation_of_energy).  The equation of
+ * state is the stiffened gas p = (gamma - 1) rho e - gamma p_inf,
+ * T = (p + p_inf) / rho, c^2 = gamma (p + p_inf) / rho, which with p_inf = 0
+ * is the ideal gas of Sec. 4 (Sec. 4 notes that the scheme takes another
+ * equation of state).
  *
  * Conventions for every call:
  *   - Arrays are structure-of-arrays: field f of cell (i, j[, k]) is at
@@ -41,7 +44,7 @@ typedef enum {
     ARK_OK = 0,
     ARK_ERR_INVALID_ARG = 1,   /* a parameter or pointer is out of its domain       */
     ARK_ERR_CUDA = 2,          /* a CUDA runtime call failed (see ark_last_error)    */
-    ARK_ERR_NONPHYSICAL = 3,   /* the device saw rho <= 0, p <= 0, L~ <= 0 or a NaN  */
+    ARK_ERR_NONPHYSICAL = 3,   /* the device saw rho <= 0, p + p_inf <= 0, L~ <= 0, NaN */
     ARK_ERR_TIMEOUT = 4,       /* a bounded wait on the device ran out               */
     ARK_ERR_UNSUPPORTED = 5,   /* valid input that this build does not implement     */
     ARK_ERR_ALLOC = 6          /* device or host allocation failed                   */
@@ -78,7 +81,10 @@ typedef struct {
 } ark_grid;
 
 typedef struct {
-    double gamma;              /* adiabatic index of the ideal gas, > 1               */
+    double gamma;              /* adiabatic index, > 1                                */
+    double p_inf;              /* stiffened-gas constant, finite and >= 0 (0: ideal
+                                  gas).  Physical states need rho > 0 and
+                                  p + p_inf > 0; p itself may be negative.            */
 } ark_eos;
 
 typedef struct {

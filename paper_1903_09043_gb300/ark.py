@@ -48,7 +48,7 @@ class ark_grid(ctypes.Structure):
 
 
 class ark_eos(ctypes.Structure):
-    _fields_ = [("gamma", ctypes.c_double)]
+    _fields_ = [("gamma", ctypes.c_double), ("p_inf", ctypes.c_double)]
 
 
 class ark_gravity(ctypes.Structure):
@@ -153,6 +153,7 @@ def params_from_problem(prob, precision: int = ARK_F64) -> ark_params:
         p.bc.T_lo[d] = float(prob.T_lo[d])
         p.bc.T_hi[d] = float(prob.T_hi[d])
     p.eos.gamma = float(prob.gamma)
+    p.eos.p_inf = float(getattr(prob, "p_inf", 0.0))
     p.gravity.g = float(prob.g)
     phi = getattr(prob, "phi", None)
     if phi is not None:   # caller-supplied potential: a host array ark_create copies

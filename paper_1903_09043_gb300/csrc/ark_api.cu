@@ -51,6 +51,7 @@ ark::StepArgs ark::base_args(const ark_handle* h)
         a.Tw_hi[d] = p.bc.T_hi[d];
     }
     a.gamma = p.eos.gamma;
+    a.p_inf = p.eos.p_inf;
     a.g = p.gravity.g;
     a.lo_v = p.grid.lo[h->dim - 1];
     a.mu = p.mu;
@@ -112,6 +113,10 @@ ark_status validate(const ark_params* p, std::string& msg)
         }
     }
     if (!(p->eos.gamma > 1.0)) { msg = "eos.gamma must be > 1"; return ARK_ERR_INVALID_ARG; }
+    if (!(p->eos.p_inf >= 0.0) || !std::isfinite(p->eos.p_inf)) {
+        msg = "eos.p_inf must be finite and >= 0";
+        return ARK_ERR_INVALID_ARG;
+    }
     if (!(p->K >= 1.0)) { msg = "K must be >= 1 (sub-characteristic condition)"; return ARK_ERR_INVALID_ARG; }
     if (!(p->cfl > 0.0)) { msg = "cfl must be > 0"; return ARK_ERR_INVALID_ARG; }
     if (!(p->mu >= 0.0) || !(p->kappa >= 0.0)) { msg = "mu and kappa must be >= 0"; return ARK_ERR_INVALID_ARG; }
@@ -324,14 +329,15 @@ ark_status ark_set_state(ark_handle* h, const double* U, int on_device)
         if (e != cudaSuccess) return cuda_fail(h, e, "base state");
         std::vector<double> rho(hm.begin(), hm.begin() + nv), pr(hm.begin() + nv, hm.end());
         for (int r = 0; r < nv; ++r)
-            if (!(rho[r] > 0.0) || !(pr[r] > 0.0)) return fail(h, ARK_ERR_NONPHYSICAL, "base state with rho <= 0 or p <= 0");
+            if (!(rho[r] > 0.0) || !(pr[r] + h->p.eos.p_inf > 0.0))
+                return fail(h, ARK_ERR_NONPHYSICAL, "base state with rho <= 0 or p + p_inf <= 0");
         std::vector<double> b64;
         std::vector<float> tab;
         {
             const ark_params& p = h->p;
             const int V = h->dim - 1;
             ark::BaseSpec bs{nv, p.grid.lo[V], (p.grid.hi[V] - p.grid.lo[V]) / nv, p.gravity.g, p.eos.gamma, p.kappa,
-                             p.bc.lo[V], p.bc.hi[V], p.bc.T_lo[V], p.bc.T_hi[V]};
+                             p.bc.lo[V], p.bc.hi[V], p.bc.T_lo[V], p.bc.T_hi[V], p.eos.p_inf};
             ark::build_base_tables(bs, rho, pr, b64, tab);
         }
         e = cudaMemcpyAsync(h->base64, b64.data(), b64.size() * sizeof(double), cudaMemcpyHostToDevice, h->stream);

@@ -27,7 +27,8 @@ __global__ void __launch_bounds__(AUX_THREADS) wave_rate_kernel(const __grid_con
     const int nv = a.n[D - 1];
     const PhiRow<Real> ph(a);
     const KConst<Real> kc(a);
-    const Real gamma = kc.gamma, gm1 = kc.gm1, mu = kc.mu, kappa = kc.kappa;
+    const Eos<Real> eos(kc);
+    const Real mu = kc.mu, kappa = kc.kappa;
     const Real invdx[3] = {kc.invdx[0], kc.invdx[1], kc.invdx[2]};
     Real smax = Real(0);
     for (long long idx = blockIdx.x * (long long)blockDim.x + threadIdx.x; idx < a.ncell;
@@ -38,7 +39,7 @@ __global__ void __launch_bounds__(AUX_THREADS) wave_rate_kernel(const __grid_con
         Row<Real> w = row_info<Real, SPLIT>(a, ph, row_of(a, idx), nv);
         if (a.phiA && !a.energy_form) w.phi = __ldg(static_cast<const Real*>(a.phiA) + idx);   // caller's Phi
         Real p, rho;
-        const Real sh = wave_rate<D, Real, SPLIT, VISC>(b, w, gm1, gamma, invdx, mu, kappa, p, rho);
+        const Real sh = wave_rate<D, Real, SPLIT, VISC>(b, w, eos, invdx, mu, kappa, p, rho);
         if (!(sh <= smax)) smax = (sh == sh) ? sh : smax;
     }
     block_rate_max(double(smax), reinterpret_cast<unsigned long long*>(red), slot);
@@ -105,7 +106,7 @@ __global__ void __launch_bounds__(AUX_THREADS) row_means_kernel(const StepArgs a
         }
         const double ke = 0.5 * m2 / rho;   // one FP64 division per cell
         accr += rho;
-        accp += (a.gamma - 1.0) * (U[(D + 1) * a.ncell + idx] - ke - rho * phi);
+        accp += (a.gamma - 1.0) * (U[(D + 1) * a.ncell + idx] - ke - rho * phi) - a.dgpinf;
     }
     sr[threadIdx.x] = accr;
     sp[threadIdx.x] = accp;
@@ -154,7 +155,7 @@ __global__ void __launch_bounds__(AUX_THREADS) diag_kernel(const StepArgs a, con
             ke += 0.5 * rho * u * u;
             u2 += u * u;
         }
-        const double p = (a.gamma - 1.0) * (W - ke - rho * phi);
+        const double p = (a.gamma - 1.0) * (W - ke - rho * phi) - a.dgpinf;
         acc[DG_MASS] += rho;
         acc[DG_MX] += m[0];
         acc[DG_MY] += m[1];

@@ -13,11 +13,14 @@ struct BaseSpec {
     double g, gamma, kappa;
     int bc_lo, bc_hi;    // boundary conditions of that axis
     double T_lo, T_hi;   // wall temperatures
+    double p_inf;        // stiffened-gas constant (0: ideal gas)
 };
 
 // FP64 base state of F32_SPLIT: rows -2 .. nv + 1 from the interior row means,
 // ghost rows by the boundary rule of the gravity axis applied to the base,
-// then every table entry formed in FP64 and rounded once.
+// then every table entry formed in FP64 and rounded once.  Pressures enter the
+// equation of state as pe = p + p_inf: T0 = pe0 / rho0, the wall balance in pe,
+// and B_P0 holds pe0.
 inline void build_base_tables(const BaseSpec& s, const std::vector<double>& rho_in, const std::vector<double>& p_in,
                               std::vector<double>& b64, std::vector<float>& tab)
 {
@@ -26,7 +29,11 @@ inline void build_base_tables(const BaseSpec& s, const std::vector<double>& rho_
     const double gm1 = s.gamma - 1.0;
     std::vector<double> rho(L), pr(L), T(L), phi(L);
     for (int r = -2; r < nv + 2; ++r) phi[r + 2] = -(s.g * (s.lo_v + (r + 0.5) * dv));
-    for (int r = 0; r < nv; ++r) { rho[r + 2] = rho_in[r]; pr[r + 2] = p_in[r]; T[r + 2] = p_in[r] / rho_in[r]; }
+    for (int r = 0; r < nv; ++r) {
+        rho[r + 2] = rho_in[r];
+        pr[r + 2] = p_in[r];
+        T[r + 2] = (p_in[r] + s.p_inf) / rho_in[r];
+    }
     for (int side = 0; side < 2; ++side) {
         const int bc = side == 0 ? s.bc_lo : s.bc_hi;
         const double Tw = side == 0 ? s.T_lo : s.T_hi;
@@ -43,8 +50,9 @@ inline void build_base_tables(const BaseSpec& s, const std::vector<double>& rho_
             } else {
                 const double Tg = bc == BC_REFLECT ? T[m + 2] : 2.0 * Tw - T[m + 2];
                 const double dphi = phi[g + 2] - phi[A + 2];
-                pr[g + 2] = (pr[A + 2] - 0.5 * rho[A + 2] * dphi) / (1.0 + dphi / (2.0 * Tg));
-                rho[g + 2] = pr[g + 2] / Tg;
+                const double pe = (pr[A + 2] + s.p_inf - 0.5 * rho[A + 2] * dphi) / (1.0 + dphi / (2.0 * Tg));
+                pr[g + 2] = pe - s.p_inf;
+                rho[g + 2] = pe / Tg;
                 T[g + 2] = Tg;
             }
         }
@@ -52,7 +60,7 @@ inline void build_base_tables(const BaseSpec& s, const std::vector<double>& rho_
     b64.assign(3 * L, 0.0);
     std::vector<double> W0(L);
     for (int i = 0; i < L; ++i) {
-        W0[i] = pr[i] / gm1 + rho[i] * phi[i];
+        W0[i] = (pr[i] + s.gamma * s.p_inf) / gm1 + rho[i] * phi[i];
         b64[0 * L + i] = rho[i];
         b64[1 * L + i] = pr[i];
         b64[2 * L + i] = W0[i];
@@ -61,7 +69,7 @@ inline void build_base_tables(const BaseSpec& s, const std::vector<double>& rho_
     auto at = [&](int f, int i) -> double& { return t[(size_t)i * BSTRIDE + f]; };   // i = r + 2
     for (int i = 0; i < L; ++i) {
         at(B_RHO0, i) = rho[i];
-        at(B_P0, i) = pr[i];
+        at(B_P0, i) = pr[i] + s.p_inf;
         at(B_T0, i) = T[i];
         at(B_H0, i) = W0[i] + pr[i];
     }

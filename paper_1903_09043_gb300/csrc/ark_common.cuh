@@ -17,9 +17,9 @@ enum Status : unsigned { ST_NONPHYS = 1u, ST_LTILDE = 2u, ST_NAN = 4u };
 // rounded once to the state precision.
 enum BaseField : int {
     B_RHO0 = 0,  // rho0_r
-    B_P0,        // p0_r
-    B_T0,        // T0_r = p0_r / rho0_r
-    B_H0,        // W0_r + p0_r, W0 = p0/(gamma-1) + rho0 Phi_r
+    B_P0,        // pe0_r = p0_r + p_inf (effective pressure of the equation of state)
+    B_T0,        // T0_r = pe0_r / rho0_r
+    B_H0,        // W0_r + p0_r, W0 = (p0 + gamma p_inf)/(gamma-1) + rho0 Phi_r
     B_R0F,       // p0_{r+1} - p0_r - S0_{r+1/2}: base residual of the face above row r
     B_Q0,        // (R0F_r + R0F_{r-1}) / 2: base part of [Pi*] - S_i in the vertical momentum
     B_DPP,       // P0_{r+1/2} - p0_r = (p0_{r+1} - p0_r) / 2
@@ -41,12 +41,13 @@ struct StepArgs {
     int n[3];               // cells per axis (x, y, z); the last active axis is the gravity axis
     double dx[3];           // cell sizes
     double gamma;
+    double p_inf;           // stiffened-gas constant (0: ideal gas)
     double g;               // gravity along the last axis: Phi = -g x_last
     double lo_v;            // lower coordinate of the last axis
     double mu, kappa, K, cfl;
     int low_mach;
-    int energy_form;
-    long long work_per_block;   // balanced schedule: (tile, plane) units per block (column kernels)        // 0: rho*calE (Sec. 2); 1: rho E with the (uS) source (Appendix B)
+    int energy_form;        // 0: rho*calE (Sec. 2); 1: rho E with the (uS) source (Appendix B)
+    long long work_per_block;   // balanced schedule: (tile, plane) units per block (column kernels)
     int bc_lo[3], bc_hi[3];
     double Tw_lo[3], Tw_hi[3];
     int planes;             // planes of the gravity axis per block
@@ -66,9 +67,9 @@ struct StepArgs {
     // constants of the stencil in both precisions, rounded once on the host, so
     // that no kernel converts between precisions (conversions run on GB300's
     // FP64 pipe, 1/64 of its FP32 rate)
-    float fK, fhalfInvK, fmu, fkappa, feta, fgamma, fgm1, fphi_g, fphi_lo, fphi_dv, finvdx[3];
+    float fK, fhalfInvK, fmu, fkappa, feta, fgamma, fgm1, fpinf, fgpinf, fphi_g, fphi_lo, fphi_dv, finvdx[3];
     float fdphi;            // Phi_{r+1} - Phi_r = -g dz, formed in FP64 (uniform g)
-    double dK, dhalfInvK, deta, dinvdx[3];
+    double dK, dhalfInvK, deta, dgpinf, dinvdx[3];
 };
 
 // Set the precomputed constants of a StepArgs whose double fields are filled.
@@ -78,6 +79,7 @@ inline void fill_constants(StepArgs& a)
     a.dK = a.K;
     a.dhalfInvK = 0.5 / a.K;
     a.deta = -2.0 / 3.0 * a.mu;
+    a.dgpinf = a.gamma * a.p_inf;
     for (int d = 0; d < 3; ++d) a.dinvdx[d] = 1.0 / a.dx[d];
     a.fK = (float)a.K;
     a.fhalfInvK = (float)a.dhalfInvK;
@@ -86,6 +88,8 @@ inline void fill_constants(StepArgs& a)
     a.feta = (float)a.deta;
     a.fgamma = (float)a.gamma;
     a.fgm1 = (float)(a.gamma - 1.0);
+    a.fpinf = (float)a.p_inf;
+    a.fgpinf = (float)a.dgpinf;
     a.fphi_g = (float)a.g;
     a.fphi_lo = (float)a.lo_v;
     a.fphi_dv = (float)a.dx[V];

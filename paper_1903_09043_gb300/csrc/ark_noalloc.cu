@@ -7,6 +7,7 @@
 // the device or fail when memory is exhausted), or an embedding runtime that
 // forbids library allocations.  This entry point needs no handle: its only
 // scratch is a fixed array in the library's own device image.
+#include <cmath>
 #include <mutex>
 
 #include "../../include/ark.h"
@@ -37,7 +38,7 @@ __global__ void __launch_bounds__(NA_THREADS) na_rate_kernel(const __grid_consta
     __shared__ double red[NA_THREADS];
     const int nv = a.n[D - 1];
     const ark::PhiRow<double> ph(a);
-    const double gm1 = a.gamma - 1.0;
+    const ark::Eos<double> eos{ark::KConst<double>(a)};
     const double invdx[3] = {1.0 / a.dx[0], 1.0 / a.dx[1], 1.0 / a.dx[2]};
     const long long plane = D == 3 ? (long long)a.n[0] * a.n[1] : (long long)a.n[0];
     double m = 0.0;
@@ -49,7 +50,7 @@ __global__ void __launch_bounds__(NA_THREADS) na_rate_kernel(const __grid_consta
         for (int f = 0; f < D + 2; ++f) b[f] = __ldg(U + f * a.ncell + idx);
         const ark::Row<double> w = ark::row_info<double, false>(a, ph, (int)(idx / plane), nv);
         double p, rho;
-        const double s = ark::wave_rate<D, double, false, VISC>(b, w, gm1, a.gamma, invdx, a.mu, a.kappa, p, rho);
+        const double s = ark::wave_rate<D, double, false, VISC>(b, w, eos, invdx, a.mu, a.kappa, p, rho);
         if (!(s <= m)) m = (s == s) ? s : m;
     }
     red[threadIdx.x] = m;
@@ -103,7 +104,9 @@ extern "C" ark_status ark_compute_dt_noalloc(const ark_params* p, const double* 
     if (dim != 2 && dim != 3) return ARK_ERR_INVALID_ARG;
     if (p->precision != ARK_F64) return ARK_ERR_INVALID_ARG;
     if (p->gravity.phi) return ARK_ERR_UNSUPPORTED;   // the potential array would need a device copy
-    if (!(p->eos.gamma > 1.0) || !(p->cfl > 0.0) || !(p->mu >= 0.0) || !(p->kappa >= 0.0)) return ARK_ERR_INVALID_ARG;
+    if (!(p->eos.gamma > 1.0) || !(p->eos.p_inf >= 0.0) || !std::isfinite(p->eos.p_inf) || !(p->cfl > 0.0) ||
+        !(p->mu >= 0.0) || !(p->kappa >= 0.0))
+        return ARK_ERR_INVALID_ARG;
     long long ncell = 1;
     ark::StepArgs a;
     memset(&a, 0, sizeof a);
@@ -121,13 +124,16 @@ extern "C" ark_status ark_compute_dt_noalloc(const ark_params* p, const double* 
     }
     if (ncell > NA_MAX_CELLS) return ARK_ERR_INVALID_ARG;   // beyond the fixed scratch
     a.gamma = p->eos.gamma;
+    a.p_inf = p->eos.p_inf;
     a.g = p->gravity.g;
     a.lo_v = p->grid.lo[dim - 1];
     a.mu = p->mu;
     a.kappa = p->kappa;
     a.cfl = p->cfl;
     a.energy_form = p->energy_form;
+    a.K = p->K;
     a.ncell = ncell;
+    ark::fill_constants(a);
 
     double* scratch = nullptr;
     if (scratch_for_current_device(&scratch) != cudaSuccess) return ARK_ERR_CUDA;

@@ -185,17 +185,32 @@ template <typename Real>
 struct KConst;
 template <>
 struct KConst<float> {
-    float K, halfInvK, mu, kappa, eta, gamma, gm1, invdx[3];
+    float K, halfInvK, mu, kappa, eta, gamma, gm1, pinf, gpinf, invdx[3];
     __device__ explicit KConst(const StepArgs& a)
         : K(a.fK), halfInvK(a.fhalfInvK), mu(a.fmu), kappa(a.fkappa), eta(a.feta), gamma(a.fgamma), gm1(a.fgm1),
-          invdx{a.finvdx[0], a.finvdx[1], a.finvdx[2]} {}
+          pinf(a.fpinf), gpinf(a.fgpinf), invdx{a.finvdx[0], a.finvdx[1], a.finvdx[2]} {}
 };
 template <>
 struct KConst<double> {
-    double K, halfInvK, mu, kappa, eta, gamma, gm1, invdx[3];
+    double K, halfInvK, mu, kappa, eta, gamma, gm1, pinf, gpinf, invdx[3];
     __device__ explicit KConst(const StepArgs& a)
         : K(a.dK), halfInvK(a.dhalfInvK), mu(a.mu), kappa(a.kappa), eta(a.deta), gamma(a.gamma), gm1(a.gamma - 1.0),
-          invdx{a.dinvdx[0], a.dinvdx[1], a.dinvdx[2]} {}
+          pinf(a.p_inf), gpinf(a.dgpinf), invdx{a.dinvdx[0], a.dinvdx[1], a.dinvdx[2]} {}
+};
+
+// Equation of state: the stiffened gas (Harlow and Amsden 1971; temperature
+// as in Le Metayer, Massoni and Saurel 2004, with (gamma-1) c_v = 1), which
+// the scheme admits as Sec. 4 notes that another equation of state may be
+// used; p_inf = 0 is the ideal gas of Sec. 4:
+//   p = (gamma-1) rho e - gamma p_inf,  T = (p + p_inf) / rho,
+//   c^2 = gamma (p + p_inf) / rho.
+// Every formula below reads the pressure either as a difference or as the
+// effective pressure pe = p + p_inf.  In F32_SPLIT the base row carries
+// pe0 = p0 + p_inf (B_P0), so deviations need no p_inf term at all.
+template <typename Real>
+struct Eos {
+    Real gamma, gm1, pinf, gpinf;   // gpinf = gamma p_inf
+    __device__ explicit Eos(const KConst<Real>& k) : gamma(k.gamma), gm1(k.gm1), pinf(k.pinf), gpinf(k.gpinf) {}
 };
 
 // Phi at the centre of row r of the gravity axis (Phi = -g x_last), in the
@@ -230,9 +245,9 @@ __device__ __forceinline__ Row<Real> row_info(const StepArgs& a, const PhiRow<Re
     return w;
 }
 
-// Primitive values from conserved values (ideal gas, Sec. 4; p = rho T).
+// Primitive values from conserved values (the equation of state above).
 template <int D, typename Real, bool SPLIT>
-__device__ __forceinline__ void prim(Cell<D, Real>& c, const Row<Real>& w, Real gm1, Real gamma)
+__device__ __forceinline__ void prim(Cell<D, Real>& c, const Row<Real>& w, const Eos<Real>& q)
 {
     c.rho = SPLIT ? w.rho0 + c.drho : c.drho;
     const Real rr = rcp(c.rho);
@@ -243,15 +258,16 @@ __device__ __forceinline__ void prim(Cell<D, Real>& c, const Row<Real>& w, Real 
         c.u[d] = c.m[d] * rr;
         ke += c.m[d] * c.u[d];
     }
-    c.dp = gm1 * (c.dW - Real(0.5) * ke - c.drho * w.phi);
-    const Real p = SPLIT ? w.p0 + c.dp : c.dp;
-    c.dT = SPLIT ? (c.dp - w.T0 * c.drho) * rr : p * rr;
-    sqrt_rsqrt(gamma * p * rr, c.c, c.rc);
+    const Real re = c.dW - Real(0.5) * ke - c.drho * w.phi;
+    c.dp = SPLIT ? q.gm1 * re : q.gm1 * re - q.gpinf;
+    const Real pe = SPLIT ? w.p0 + c.dp : c.dp + q.pinf;
+    c.dT = SPLIT ? (c.dp - w.T0 * c.drho) * rr : pe * rr;
+    sqrt_rsqrt(q.gamma * pe * rr, c.c, c.rc);
 }
 
 // Conserved values of a ghost built from primitives (rho full, u, dp, dT).
 template <int D, typename Real, bool SPLIT>
-__device__ __forceinline__ void cons_from_prim(Cell<D, Real>& g, const Row<Real>& w, Real gm1, Real gamma)
+__device__ __forceinline__ void cons_from_prim(Cell<D, Real>& g, const Row<Real>& w, const Eos<Real>& q)
 {
     Real ke = Real(0);
 #pragma unroll
@@ -259,23 +275,26 @@ __device__ __forceinline__ void cons_from_prim(Cell<D, Real>& g, const Row<Real>
         g.m[d] = g.rho * g.u[d];
         ke += g.rho * g.u[d] * g.u[d];
     }
-    g.dW = g.dp / gm1 + Real(0.5) * ke + g.drho * w.phi;
-    const Real p = SPLIT ? w.p0 + g.dp : g.dp;
+    // rho e = (p + gamma p_inf) / (gamma - 1); the deviation form cancels gamma p_inf
+    g.dW = (SPLIT ? g.dp : g.dp + q.gpinf) / q.gm1 + Real(0.5) * ke + g.drho * w.phi;
+    const Real pe = SPLIT ? w.p0 + g.dp : g.dp + q.pinf;
     g.rr = rcp(g.rho);
-    sqrt_rsqrt(gamma * p * g.rr, g.c, g.rc);
+    sqrt_rsqrt(q.gamma * pe * g.rr, g.c, g.rc);
 }
 
 // Wall ghost (reflective hydrostatic or no-slip fixed-temperature): velocity
 // mirrored (normal component, or all components, with sign flip);
 // temperature mirrored or reflected about the wall value; pressure from the
-// discrete hydrostatic balance of Eq. 18 with the inner neighbour A, written
-// in deviation form: with base ghost row (rho0_g, T0_g) built by the same rule,
+// discrete hydrostatic balance of Eq. 18 with the inner neighbour A, in the
+// effective pressure pe = p + p_inf (rho = pe / T):
+//   pe_g = (pe_A - dPhi rho_A / 2) / (1 + dPhi / (2 T_g)),  rho_g = pe_g / T_g;
+// in deviation form, with base ghost row (rho0_g, T0_g) built by the same rule,
 //   dp_g = (dp_A - dPhi drho_A / 2 + dPhi rho0_g dT_g / (2 T_g)) / (1 + dPhi / (2 T_g)),
 //   drho_g = (dp_g - rho0_g dT_g) / T_g.
 template <int D, typename Real, bool SPLIT>
 __device__ __forceinline__ Cell<D, Real> wall_ghost(const Cell<D, Real>& M, const Cell<D, Real>& A, int bc,
                                                     int axis, Real Tw, const Row<Real>& wg, Real dphi,
-                                                    Real gm1, Real gamma)
+                                                    const Eos<Real>& q)
 {
     Cell<D, Real> g;
 #pragma unroll
@@ -284,23 +303,25 @@ __device__ __forceinline__ Cell<D, Real> wall_ghost(const Cell<D, Real>& M, cons
     if (bc == BC_REFLECT) dTg = M.dT;
     else dTg = SPLIT ? -M.dT : Real(2) * Tw - M.dT;
     const Real Tg = SPLIT ? wg.T0 + dTg : dTg;
-    Real num = A.dp - Real(0.5) * A.drho * dphi;
+    Real num = (SPLIT ? A.dp : A.dp + q.pinf) - Real(0.5) * A.drho * dphi;
     if constexpr (SPLIT) num += Real(0.5) * wg.rho0 * dphi * dTg / Tg;
-    g.dp = num / (Real(1) + dphi / (Real(2) * Tg));
-    g.drho = SPLIT ? (g.dp - wg.rho0 * dTg) / Tg : g.dp / Tg;
+    const Real x = num / (Real(1) + dphi / (Real(2) * Tg));   // dp_g (split) or pe_g
+    g.dp = SPLIT ? x : x - q.pinf;
+    g.drho = SPLIT ? (x - wg.rho0 * dTg) / Tg : x / Tg;
     g.dT = dTg;
     g.rho = SPLIT ? wg.rho0 + g.drho : g.drho;
-    cons_from_prim<D, Real, SPLIT>(g, wg, gm1, gamma);
+    cons_from_prim<D, Real, SPLIT>(g, wg, q);
     return g;
 }
 
 // CFL wave rate of one cell (the time step is cfl / max over cells):
 //   max( sum_d (|u_d| + c) / dx_d , sum_d 2 max(4 mu / (3 rho), kappa (gamma-1) / rho) / dx_d^2 ).
-// b holds the cell's stored values (deviation form in F32_SPLIT); p and rho
-// are returned for the physical checks.
+// b holds the cell's stored values (deviation form in F32_SPLIT); the
+// effective pressure pe = p + p_inf and rho are returned for the physical
+// checks (both must be positive).
 template <int D, typename Real, bool SPLIT, bool VISC>
-__device__ __forceinline__ Real wave_rate(const Real* b, const Row<Real>& w, Real gm1, Real gamma,
-                                          const Real* invdx, Real mu, Real kappa, Real& p, Real& rho)
+__device__ __forceinline__ Real wave_rate(const Real* b, const Row<Real>& w, const Eos<Real>& q,
+                                          const Real* invdx, Real mu, Real kappa, Real& pe, Real& rho)
 {
     rho = SPLIT ? w.rho0 + b[0] : b[0];
     const Real rr = rcp(rho);
@@ -311,14 +332,15 @@ __device__ __forceinline__ Real wave_rate(const Real* b, const Row<Real>& w, Rea
         uu[d] = b[1 + d] * rr;
         ke += b[1 + d] * uu[d];
     }
-    const Real dp = gm1 * (b[D + 1] - Real(0.5) * ke - b[0] * w.phi);
-    p = SPLIT ? w.p0 + dp : dp;
+    const Real re = b[D + 1] - Real(0.5) * ke - b[0] * w.phi;
+    const Real dp = SPLIT ? q.gm1 * re : q.gm1 * re - q.gpinf;
+    pe = SPLIT ? w.p0 + dp : dp + q.pinf;
     Real cs, rcs;
-    sqrt_rsqrt(gamma * p * rr, cs, rcs);
+    sqrt_rsqrt(q.gamma * pe * rr, cs, rcs);
 #pragma unroll
     for (int d = 0; d < D; ++d) sh += (vabs(uu[d]) + cs) * invdx[d];
     if constexpr (VISC) {
-        const Real nu = Real(4.0 / 3.0) * mu * rr, chi = kappa * gm1 * rr;
+        const Real nu = Real(4.0 / 3.0) * mu * rr, chi = kappa * q.gm1 * rr;
         const Real dm = pmax(nu, chi);
         Real s2 = Real(0);   // sum_d 2 / dx_d^2 (loop-invariant)
 #pragma unroll
@@ -373,18 +395,15 @@ struct Stepper {
     long long N;
     int nx, ny, nv;
     PhiRow<Real> phi;
-    Real gm1, gamma;
+    Eos<Real> eos;
 
-    __device__ Stepper(const StepArgs& args) : a(args), phi(args)
+    __device__ Stepper(const StepArgs& args) : a(args), phi(args), eos(KConst<Real>(args))
     {
         U = static_cast<const Real*>(a.Uin);
         N = a.ncell;
         nx = a.n[0];
         ny = D == 3 ? a.n[1] : 1;
         nv = a.n[V];
-        const KConst<Real> kc(a);
-        gamma = kc.gamma;
-        gm1 = kc.gm1;
     }
 
     // Phi at (gx, gy, gv) (ghosts included), in the state precision
@@ -416,7 +435,7 @@ struct Stepper {
 #pragma unroll
         for (int d = 0; d < D; ++d) c.m[d] = __ldg(U + (1 + d) * N + idx);
         c.dW = __ldg(U + (D + 1) * N + idx);
-        prim<D, Real, SPLIT>(c, at(w, gx, gy, gv), gm1, gamma);
+        prim<D, Real, SPLIT>(c, at(w, gx, gy, gv), eos);
         return c;
     }
 
@@ -432,19 +451,19 @@ struct Stepper {
         if (bc == BC_PERIODIC) return load_in(((gx % nx) + nx) % nx, gy, gv, w);
         if (bc == BC_OUTFLOW) {
             Cell<D, Real> M = load_in(lo ? 0 : nx - 1, gy, gv, w);
-            if constexpr (PHIA) cons_from_prim<D, Real, SPLIT>(M, at(w, gx, gy, gv), gm1, gamma);
+            if constexpr (PHIA) cons_from_prim<D, Real, SPLIT>(M, at(w, gx, gy, gv), eos);
             return M;
         }
         const Real Tw = Real(lo ? a.Tw_lo[0] : a.Tw_hi[0]);
         const int x0 = lo ? 0 : nx - 1, x1 = lo ? 1 : nx - 2, g1 = lo ? -1 : nx;
         const Cell<D, Real> M0 = load_in(x0, gy, gv, w);
         const Real d1 = PHIA ? phi_cell(g1, gy, gv) - phi_cell(x0, gy, gv) : Real(0);
-        Cell<D, Real> g1c = wall_ghost<D, Real, SPLIT>(M0, M0, bc, 0, Tw, at(w, g1, gy, gv), d1, gm1, gamma);
+        Cell<D, Real> g1c = wall_ghost<D, Real, SPLIT>(M0, M0, bc, 0, Tw, at(w, g1, gy, gv), d1, eos);
         const int layer = lo ? -gx : gx - nx + 1;
         if (layer == 1) return g1c;
         const Cell<D, Real> M1 = load_in(x1, gy, gv, w);
         const Real d2 = PHIA ? phi_cell(gx, gy, gv) - phi_cell(g1, gy, gv) : Real(0);
-        return wall_ghost<D, Real, SPLIT>(M1, g1c, bc, 0, Tw, at(w, gx, gy, gv), d2, gm1, gamma);
+        return wall_ghost<D, Real, SPLIT>(M1, g1c, bc, 0, Tw, at(w, gx, gy, gv), d2, eos);
     }
 
     __device__ Cell<D, Real> fetch_h(int gx, int gy, int gv, const Row<Real>& w) const
@@ -456,19 +475,19 @@ struct Stepper {
                 if (bc == BC_PERIODIC) return fetch_x(gx, ((gy % ny) + ny) % ny, gv, w);
                 if (bc == BC_OUTFLOW) {
                     Cell<D, Real> M = fetch_x(gx, lo ? 0 : ny - 1, gv, w);
-                    if constexpr (PHIA) cons_from_prim<D, Real, SPLIT>(M, at(w, gx, gy, gv), gm1, gamma);
+                    if constexpr (PHIA) cons_from_prim<D, Real, SPLIT>(M, at(w, gx, gy, gv), eos);
                     return M;
                 }
                 const Real Tw = Real(lo ? a.Tw_lo[1] : a.Tw_hi[1]);
                 const int y0 = lo ? 0 : ny - 1, y1 = lo ? 1 : ny - 2, g1 = lo ? -1 : ny;
                 const Cell<D, Real> M0 = fetch_x(gx, y0, gv, w);
                 const Real d1 = PHIA ? phi_cell(gx, g1, gv) - phi_cell(gx, y0, gv) : Real(0);
-                Cell<D, Real> g1c = wall_ghost<D, Real, SPLIT>(M0, M0, bc, 1, Tw, at(w, gx, g1, gv), d1, gm1, gamma);
+                Cell<D, Real> g1c = wall_ghost<D, Real, SPLIT>(M0, M0, bc, 1, Tw, at(w, gx, g1, gv), d1, eos);
                 const int layer = lo ? -gy : gy - ny + 1;
                 if (layer == 1) return g1c;
                 const Cell<D, Real> M1 = fetch_x(gx, y1, gv, w);
                 const Real d2 = PHIA ? phi_cell(gx, gy, gv) - phi_cell(gx, g1, gv) : Real(0);
-                return wall_ghost<D, Real, SPLIT>(M1, g1c, bc, 1, Tw, at(w, gx, gy, gv), d2, gm1, gamma);
+                return wall_ghost<D, Real, SPLIT>(M1, g1c, bc, 1, Tw, at(w, gx, gy, gv), d2, eos);
             }
         }
         return fetch_x(gx, gy, gv, w);
@@ -490,7 +509,7 @@ struct Stepper {
             const int s = lo ? 0 : nv - 1;
             Cell<D, Real> M = fetch_h(gx, gy, s, row_info<Real, SPLIT>(a, phi, s, nv));
             Cell<D, Real> g = M;   // (rho, u, p) copied; base rows of an outflow ghost copy the edge row
-            cons_from_prim<D, Real, SPLIT>(g, at(wg, gx, gy, gv), gm1, gamma);
+            cons_from_prim<D, Real, SPLIT>(g, at(wg, gx, gy, gv), eos);
             return g;
         }
         const Real Tw = Real(lo ? a.Tw_lo[V] : a.Tw_hi[V]);
@@ -499,12 +518,12 @@ struct Stepper {
         const Row<Real> w1g = row_info<Real, SPLIT>(a, phi, g1r, nv);
         const Cell<D, Real> M0 = fetch_h(gx, gy, r0, w0);
         const Real dphi1 = phi_cell(gx, gy, g1r) - phi_cell(gx, gy, r0);
-        Cell<D, Real> g1 = wall_ghost<D, Real, SPLIT>(M0, M0, bc, V, Tw, at(w1g, gx, gy, g1r), dphi1, gm1, gamma);
+        Cell<D, Real> g1 = wall_ghost<D, Real, SPLIT>(M0, M0, bc, V, Tw, at(w1g, gx, gy, g1r), dphi1, eos);
         if (gv == g1r) return g1;
         const Row<Real> w1 = row_info<Real, SPLIT>(a, phi, r1, nv);
         const Cell<D, Real> M1 = fetch_h(gx, gy, r1, w1);
         const Real dphi2 = phi_cell(gx, gy, gv) - phi_cell(gx, gy, g1r);
-        return wall_ghost<D, Real, SPLIT>(M1, g1, bc, V, Tw, at(wg, gx, gy, gv), dphi2, gm1, gamma);
+        return wall_ghost<D, Real, SPLIT>(M1, g1, bc, V, Tw, at(wg, gx, gy, gv), dphi2, eos);
     }
 };
 
@@ -733,7 +752,7 @@ __device__ __forceinline__ void step_block(const StepArgs& a, const int tile, co
                     x.dW = raw[s][D + 1];
                     Row<Real> w = wf;
                     if constexpr (PHIA) w.phi = a.energy_form ? Real(0) : rawphi[s];
-                    prim<D, Real, SPLIT>(x, w, S.gm1, S.gamma);
+                    prim<D, Real, SPLIT>(x, w, S.eos);
                     store_cell<C, D, Real>(x, vT_f, ff_f, uc_f, c, lx, ly);
                     if constexpr (PHIA) {
                         ph_f[c] = x.rho;
@@ -1045,7 +1064,7 @@ __device__ __forceinline__ void step_block(const StepArgs& a, const int tile, co
                 Row<Real> w = row_info<Real, SPLIT>(a, S.phi, q, nv, fr - Real(2));
                 if constexpr (PHIA) w.phi = a.energy_form ? Real(0) : __ldg(Pa + idx);
                 Real p, rho;
-                const Real sh = wave_rate<D, Real, SPLIT, VISC>(nb, w, S.gm1, S.gamma, invdx, mu, kappa, p, rho);
+                const Real sh = wave_rate<D, Real, SPLIT, VISC>(nb, w, S.eos, invdx, mu, kappa, p, rho);
                 if (!(sh <= smax_t)) smax_t = (sh == sh) ? sh : smax_t;
                 if (sh != sh || p != p) status |= ST_NAN;
                 if (!(rho > Real(0)) || !(p > Real(0))) status |= ST_NONPHYS;

@@ -284,7 +284,7 @@ __device__ __forceinline__ void step_block2(const StepArgs& a, const int tile, c
 #pragma unroll
                 for (int d = 0; d < D; ++d) cc.m[d] = raw[1 + d];
                 cc.dW = raw[D + 1];
-                prim<D, Real, SPLIT>(cc, w, S.gm1, S.gamma);
+                prim<D, Real, SPLIT>(cc, w, S.eos);
             } else {
                 cc = S.fetch(gx, gy, f);
                 if constexpr (PHIA) ccphi = S.phi_cell(gx, gy, f);
@@ -581,7 +581,7 @@ __device__ __forceinline__ void step_block2(const StepArgs& a, const int tile, c
                 w.T0 = SPLIT ? Real(b20.z) : Real(0);
                 w.phi = a.energy_form ? Real(0) : (PHIA ? phi2 : S.phi.at(fr - Real(2)));
                 Real p, rho;
-                const Real sh = wave_rate<D, Real, SPLIT, VISC>(nb, w, S.gm1, S.gamma, kc.invdx, kc.mu, kc.kappa, p, rho);
+                const Real sh = wave_rate<D, Real, SPLIT, VISC>(nb, w, S.eos, kc.invdx, kc.mu, kc.kappa, p, rho);
                 if (!(sh <= smax_t)) smax_t = (sh == sh) ? sh : smax_t;
                 if (sh != sh || p != p) status |= ST_NAN;
                 if (!(rho > Real(0)) || !(p > Real(0))) status |= ST_NONPHYS;

@@ -25,8 +25,9 @@ def sound_speed(prob, U):
     phi = prob.potential()
     if getattr(prob, "energy_form", 0) == 1:
         phi = 0.0 * phi   # rho E holds no potential energy (Appendix B)
-    p = (prob.gamma - 1.0) * (U[dim + 1] - ke - rho * phi)
-    return np.sqrt(prob.gamma * np.abs(p) / rho)
+    p_inf = getattr(prob, "p_inf", 0.0)
+    p = (prob.gamma - 1.0) * (U[dim + 1] - ke - rho * phi) - prob.gamma * p_inf
+    return np.sqrt(prob.gamma * np.abs(p + p_inf) / rho)
 
 
 def floors(prob, U):

@@ -50,6 +50,9 @@ def _params(ark, **kw):
 @pytest.mark.parametrize("mutate,status", [
     (lambda p: setattr(p.grid, "dim", 4), 1),
     (lambda p: setattr(p.eos, "gamma", 1.0), 1),
+    (lambda p: setattr(p.eos, "p_inf", -1.0), 1),
+    (lambda p: setattr(p.eos, "p_inf", float("inf")), 1),
+    (lambda p: setattr(p.eos, "p_inf", float("nan")), 1),
     (lambda p: setattr(p, "K", 0.5), 1),
     (lambda p: setattr(p, "cfl", 0.0), 1),
     (lambda p: setattr(p, "mu", -1.0), 1),

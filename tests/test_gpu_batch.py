@@ -93,8 +93,10 @@ def test_batch_runs_must_stay_in_lockstep():
 
 
 def test_batch_of_atmospheres_stays_at_rest():
+    """Runs keep their own equation of state: the middle one is a stiffened-gas
+    column (p_inf = 5) among ideal-gas atmospheres."""
     from paper_1903_09043_gb300 import ark
-    runs = [I.atmosphere((n, n // 2 + 3)) for n in (64, 100, 130)]
+    runs = [I.atmosphere((n, n // 2 + 3), p_inf=pinf) for n, pinf in ((64, 0.0), (100, 5.0), (130, 0.0))]
     with ark.Batch([p for p, _ in runs], "f32split", stream=_stream()) as b:
         for i, (_, U) in enumerate(runs):
             b.set_state(i, U)

@@ -435,3 +435,66 @@ def test_potential_array_unsupported_precisions(precision):
     with pytest.raises(ark.ArkError) as ei:
         ark.Solver(prob, precision, stream=_stream())
     assert ei.value.status == ark.ARK_ERR_UNSUPPORTED
+
+
+# --------------------------------------------------------------------------
+# stiffened-gas equation of state (p_inf > 0)
+# --------------------------------------------------------------------------
+def _sg_potential_case():
+    prob, U = I.periodic_potential_state(2, (40, 24), mu=0.01, kappa=0.01)
+    prob = prob.replace(p_inf=4.0)
+    U = np.array(U)
+    U[prob.dim + 1] += 4.0 * prob.gamma / (prob.gamma - 1.0)
+    return prob, U
+
+
+STIFFENED_CASES = {
+    "2d_liquid_column_ragged": lambda: I.atmosphere((37, 29), p_inf=5.0),
+    "2d_tube_x_outflow": lambda: I.sod(64, gamma=4.4, p_inf=6.0, left=(1.0, 8.0), right=(0.8, 0.1)),
+    "2d_tube_y_outflow": lambda: I.sod(64, gamma=4.4, p_inf=6.0, left=(1.0, 8.0), right=(0.8, 0.1), axis=1),
+    "2d_strat_noslip_visc_three_tiles": lambda: I.stratified_random(2, (530, 7), mu=0.01, kappa=0.01, p_inf=3.0),
+    "2d_strat_reflect_theta1": lambda: I.stratified_random(2, (9, 14), walls=I.REFLECT_HYDRO, p_inf=2.0,
+                                                           low_mach=0),
+    "3d_strat_reflect": lambda: I.stratified_random(3, (19, 6, 8), walls=I.REFLECT_HYDRO, p_inf=2.0),
+    "3d_multi_tile_visc": lambda: I.stratified_random(3, (35, 33, 12), mu=0.005, kappa=0.005, p_inf=4.0),
+}
+
+
+@pytest.mark.parametrize("case", sorted(STIFFENED_CASES))
+@pytest.mark.parametrize("precision", ["f64", "f32", "f32split"])
+def test_stiffened_gas_matches_oracle(case, precision):
+    """Stiffened gas (p_inf > 0): every boundary rule, one to three tiles,
+    with and without dissipation, in all three precision forms."""
+    prob, U = STIFFENED_CASES[case]()
+    n = 20
+    ref, t_ref, dts = O.run(prob, U, n, return_dt=True)
+    V, d = gpu_run(prob, U, n, precision=precision)
+    errs = field_errors(prob, V, ref)
+    assert max(errs) <= (F64_TOL if precision == "f64" else n * F32_STEP_TOL), errs
+    assert d["status"] == 0
+    assert d["dt"] == pytest.approx(dts[-1], rel=1e-13 if precision == "f64" else 1e-5)
+
+
+@pytest.mark.parametrize("precision", ["f64", "f32"])
+def test_stiffened_gas_with_potential_array_and_appendix_b(precision):
+    for prob, U in (_sg_potential_case(), I.to_energy_form(*STIFFENED_CASES["3d_multi_tile_visc"](), 1)):
+        n = 20
+        ref, _ = O.run(prob, U, n)
+        V, d = gpu_run(prob, U, n, precision=precision)
+        errs = field_errors(prob, V, ref)
+        assert max(errs) <= (F64_TOL if precision == "f64" else n * F32_STEP_TOL), errs
+        assert d["status"] == 0
+
+
+def test_stiffened_liquid_column_at_rest_under_tension():
+    """A stiffened-gas column in discrete equilibrium whose upper part has
+    p < 0 < p + p_inf: 1000 steps at rest in FP64 and in the split form (whose
+    base carries pe0 = p0 + p_inf); no physical-state flag is raised."""
+    prob, U = I.atmosphere((64, 96), p_inf=5.0)
+    V, d = gpu_run(prob, U, 1000)
+    assert d["min_p"] < 0.0
+    assert d["max_speed"] < 1e-12
+    assert d["status"] == 0
+    _, ds = gpu_run(prob, U, 1000, precision="f32split")
+    assert ds["max_speed"] < 1e-10
+    assert ds["status"] == 0
