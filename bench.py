@@ -49,6 +49,8 @@ ALG_FLOPS = {(3, True): 392, (3, False): 213, (2, True): 225, (2, False): 144}
 # x 2 (FMA) x 2.07 GHz; FP64: 152 SMs x 2 FP64 FMA per clock x 2 x 2.07 GHz.
 SMS, SM_GHZ = 152, 2.07
 ALU_PEAK_TFLOPS = {"f32": SMS * 128 * 2 * SM_GHZ / 1e3, "f64": SMS * 2 * 2 * SM_GHZ / 1e3}
+# instruction issue peak: 4 schedulers per SM, one warp instruction each per clock
+ISSUE_PEAK_GWARP = SMS * 4 * SM_GHZ
 
 
 # 2D roofline line: the Rayleigh-Benard layer of Sec. 4.5 (2D polytrope m = 1.3,
@@ -80,8 +82,9 @@ def measured_peaks():
         return {"hbm_gbs": 6800.0, "bf16_tflops": 1900.0}, "fallback"
 
 
-def kernel_traffic(path):
-    """DRAM bytes per launch of the step kernel from the committed ncu figures
+def kernel_traffic(path, key="bytes_per_launch_full"):
+    """DRAM bytes per launch of the step kernel (or, with ``key``, another
+    recorded figure) from the committed ncu figures
     (profiles/step_kernel_traffic.txt), valid only while the step kernel
     sources are unchanged (their hash is recorded with the figures)."""
     import hashlib
@@ -98,7 +101,7 @@ def kernel_traffic(path):
                 h.update(g.read())
         if rec.get("source_sha256") != h.hexdigest():
             return None
-        v = rec.get(f"{path}.bytes_per_launch_full")
+        v = rec.get(f"{path}.{key}")
         return float(v) if v is not None else None
     except Exception:
         return None
@@ -408,13 +411,21 @@ def main():
         flops = ALG_FLOPS[(pprob.dim, pprob.mu > 0 or pprob.kappa > 0)]
         tflops = cells * flops / (ms * 1e-3) / 1e12
         alu_peak = ALU_PEAK_TFLOPS[dt_kind]
+        wipc = kernel_traffic(path, "warp_inst_per_cell")
+        issue = None
+        if wipc is not None:
+            gw = wipc * cells / (ms * 1e-3) / 1e9
+            issue = {"achieved": gw, "peak": ISSUE_PEAK_GWARP, "unit": "G warp-instructions/s",
+                     "frac": gw / ISSUE_PEAK_GWARP, "warp_inst_per_cell": wipc,
+                     "peak_kind": "4 issue slots per SM per clock at the maximum SM clock; instructions per cell from ncu"}
         results[path] = {
             "value": cells * world / (ms_max * 1e-3), "ms_per_step": ms_max, "dtype": dt_kind,
             "roofline": {"bound": "alu", "achieved": tflops, "peak": alu_peak, "unit": "TFLOP/s",
                          "frac": tflops / alu_peak, "traffic": traffic, "alg_flops_per_cell": flops,
                          "peak_kind": f"{dt_kind.upper()} peak from unit counts and the maximum SM clock",
                          "hbm": {"achieved": achieved, "peak": hbm, "unit": "GB/s", "frac": achieved / hbm,
-                                 "alg_bytes_per_cell": B, "peak_kind": f"{peak_kind} hbm_gbs (burst copy)"}},
+                                 "alg_bytes_per_cell": B, "peak_kind": f"{peak_kind} hbm_gbs (burst copy)"},
+                         "issue": issue},
             "launch": shape, "final_t": d["t"], "final_dt": d["dt"], "status": d["status"], "clocks": clocks,
             "workload": (WORKLOAD_2D if kind == "2d" else wl)["workload"],
         }

@@ -95,7 +95,7 @@ struct Row {
 // the relative error, so two leave it below 2^-88 and the result is within one
 // ulp of the correctly rounded value, at a fraction of the FP64-pipe work of
 // the IEEE division and square root.  Arguments are positive normal numbers
-// (densities, L~, gamma p / rho); zero, infinite or NaN arguments give NaN,
+// (densities, L~, gamma (p + p_inf) / rho); zero, infinite or NaN arguments give NaN,
 // which the step's status word reports.
 // FP32: the hardware approximations (within 2 ulp), one special-function
 // instruction each; the FP32 forms' error budget is several ulp per step.
