@@ -62,6 +62,9 @@ def _params(ark, **kw):
     (lambda p: p.bc.lo.__setitem__(0, 1), 1),                       # periodic pair broken
     (lambda p: (p.bc.lo.__setitem__(1, 0), p.bc.hi.__setitem__(1, 0)), 1),   # gravity along periodic axis
     (lambda p: p.grid.n.__setitem__(1, 1), 1),                       # wall axis with one cell
+    (lambda p: p.grid.n.__setitem__(0, 0), 1),                       # empty grid
+    (lambda p: (setattr(p, "precision", 1), p.grid.n.__setitem__(0, 65536),
+                p.grid.n.__setitem__(1, 65536)), 5),                 # 2^32 cells: beyond 32-bit FP32 offsets
     (lambda p: p.bc.T_lo.__setitem__(1, 0.0), 1),                    # non-positive wall temperature
     (lambda p: (setattr(p, "precision", 2), p.bc.lo.__setitem__(0, 2), p.bc.hi.__setitem__(0, 2),
                 p.bc.T_lo.__setitem__(0, 1.0), p.bc.T_hi.__setitem__(0, 1.0)), 5),

@@ -298,6 +298,22 @@ def test_split_low_mach_gresho_accuracy():
     assert out["f32"] > 10 * out["f32split"]
 
 
+def test_zero_steps_leave_the_state_and_clock_unchanged():
+    ark = _ark()
+    prob, U = I.stratified_random(2, (17, 11), mu=0.01, kappa=0.02)
+    for precision in ("f64", "f32split"):
+        with ark.Solver(prob, precision, stream=_stream()) as s:
+            s.set_state(U)
+            before = s.get_state()
+            s.step(0)
+            assert np.array_equal(s.get_state(), before)
+            d = s.diagnostics()
+            assert d["t"] == 0.0 and d["step"] == 0
+            with pytest.raises(ark.ArkError) as ei:
+                s.step(-1)
+            assert ei.value.status == ark.ARK_ERR_INVALID_ARG
+
+
 def test_run_twice_bitwise_identical():
     prob, U = I.stratified_random(3, (35, 33, 12), mu=0.005, kappa=0.005)
     A, da = gpu_run(prob, U, 30)
