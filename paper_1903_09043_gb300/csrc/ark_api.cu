@@ -61,7 +61,6 @@ ark::StepArgs ark::base_args(const ark_handle* h)
     a.low_mach = p.low_mach;
     a.energy_form = p.energy_form;
     a.work_per_block = h->work_per_block;
-    a.rr_rounds = h->rr_rounds;
     a.phiA = h->phiA;
     a.planes = h->planes;
     a.tiles_x = h->tiles_x;
@@ -163,22 +162,16 @@ void choose_launch(ark_handle* h, int nsm)
     const int tiles = h->tiles_x * h->tiles_y;
     const int nv = nv_of(h);
     if (h->kinfo.balanced) {
-        // one wave of resident blocks.  First R = tiles / resident rounds of
-        // whole tiles dealt round-robin (block b takes tiles b, b + resident,
-        // ...), so that neighbouring tiles run together and share their halo
-        // columns in L2; then block b takes units [b W, (b + 1) W) of the
-        // tile-major list of the leftover tiles' (tile, plane) units, as runs of
-        // planes per tile.  W >= 16 keeps the pipeline warm-up (4 fronts per
-        // run) small.
+        // one wave of resident blocks; block b takes units [b W, (b + 1) W) of the
+        // tile-major list of (tile, plane) units, as runs of planes per tile.
+        // W >= 16 keeps the pipeline warm-up (4 fronts per run) small.
+        const long long total = (long long)tiles * nv;
         const long long resident = (long long)nsm * h->kinfo.blocks_per_sm;
-        const long long R = tiles / resident;
-        const long long left = ((long long)tiles - R * resident) * nv;
-        long long W = (left + resident - 1) / resident;
-        if (left > 0 && W < 16) W = 16;
-        h->rr_rounds = (int)R;
+        long long W = (total + resident - 1) / resident;
+        if (W < 16) W = 16;
         h->work_per_block = W;
-        h->planes = (int)(R > 0 || W >= nv ? nv : W);
-        h->grid = dim3((unsigned)(R > 0 ? resident : (left + W - 1) / W), 1, 1);
+        h->planes = (int)(W < nv ? W : nv);
+        h->grid = dim3((unsigned)((total + W - 1) / W), 1, 1);
         return;
     }
     // enough blocks for ~4 waves of resident blocks, each marching >= 8 planes

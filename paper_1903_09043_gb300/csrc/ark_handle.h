@@ -32,7 +32,6 @@ struct ark_handle {
     dim3 grid;
     int planes = 1, tiles_x = 1, tiles_y = 1;
     long long work_per_block = 0;  // balanced schedule only
-    int rr_rounds = 0;             // balanced schedule only
     std::string err;
 };
 

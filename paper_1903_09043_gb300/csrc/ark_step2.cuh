@@ -639,22 +639,13 @@ template <int DIM, typename Real, bool SPLIT, bool VISC, int R2X, int R2Y, bool 
 __global__ void __launch_bounds__(R2X * R2Y, 512 / (R2X * R2Y)) ark_step2_kernel(const __grid_constant__ StepArgs a)
 {
     extern __shared__ __align__(16) unsigned char smem_raw[];
+    // balanced schedule: this block's share of the tile-major (tile, plane) units,
+    // marched as one run of planes per tile it touches
     const int nv = a.n[DIM - 1];
     const long long total = (long long)a.tiles_x * a.tiles_y * nv;
-    bool lead = blockIdx.x == 0;
-    // balanced schedule, part 1: whole tiles dealt round-robin, so that the
-    // blocks running together hold neighbouring tiles and the halo columns
-    // they share are read from DRAM once and hit in L2 for the neighbour
-    for (int r = 0; r < a.rr_rounds; ++r) {
-        step_block2<DIM, Real, SPLIT, VISC, R2X, R2Y, PHIA>(a, (int)blockIdx.x + r * (int)gridDim.x, 0, nv, lead,
-                                                           smem_raw);
-        lead = false;
-        __syncthreads();   // the next run reuses the shared exchange arrays
-    }
-    // part 2: the tiles left over, as equal shares of their tile-major
-    // (tile, plane) units, marched as one run of planes per tile touched
-    long long u = (long long)a.rr_rounds * gridDim.x * nv + (long long)blockIdx.x * a.work_per_block;
+    long long u = (long long)blockIdx.x * a.work_per_block;
     const long long end = min(u + a.work_per_block, total);
+    bool lead = blockIdx.x == 0;
     while (u < end) {
         const int tile = (int)(u / nv);
         const int z0 = (int)(u - (long long)tile * nv);

@@ -58,8 +58,8 @@ CASES = {
     "3d_strat_noslip_visc_ragged": lambda: I.stratified_random(3, (7, 18, 9), mu=0.01, kappa=0.02),
     "3d_strat_reflect": lambda: I.stratified_random(3, (19, 6, 8), walls=I.REFLECT_HYDRO),
     "3d_multi_tile": lambda: I.stratified_random(3, (35, 33, 12), mu=0.005, kappa=0.005),
-    # 12 x 13 = 156 FP32 tiles: one round-robin round on 152 SMs, then 4 tiles shared out
-    "3d_round_robin_and_leftover": lambda: I.stratified_random(3, (336, 156, 6), mu=0.005, kappa=0.005),
+    # 12 x 13 = 156 FP32 tiles shared out over 59 blocks of 16 (tile, plane) units
+    "3d_many_tiles": lambda: I.stratified_random(3, (336, 156, 6), mu=0.005, kappa=0.005),
     "3d_rb": lambda: I.rayleigh_benard(3, (20, 20, 10), amp=1e-3),
     "2d_rb_chi21": lambda: I.rayleigh_benard(2, (40, 24), chi=21.0, amp=1e-3),
     "3d_rb_chi21": lambda: I.rayleigh_benard(3, (14, 12, 24), chi=21.0, m=1.3, amp=1e-3),
@@ -234,7 +234,7 @@ def test_full_size_3d_rb_sampled(precision):
 
 
 @pytest.mark.parametrize("case", ["2d_periodic_visc", "2d_strat_noslip_visc", "3d_strat_noslip_visc_ragged", "3d_rb",
-                                  "2d_rb_chi21", "3d_rb_chi21", "2d_rayleigh_taylor", "3d_round_robin_and_leftover"])
+                                  "2d_rb_chi21", "3d_rb_chi21", "2d_rayleigh_taylor", "3d_many_tiles"])
 @pytest.mark.parametrize("precision", ["f32", "f32split"])
 def test_fp32_forms_match_oracle_within_budget(case, precision):
     prob, U = CASES[case]()
