@@ -103,3 +103,30 @@ def test_batch_of_atmospheres_stays_at_rest():
         b.step(300)
         for i in range(len(runs)):
             assert b.diagnostics(i)["max_speed"] < 1e-10
+
+
+def test_full_ensemble_sampled_against_the_oracle():
+    """The benchmark's ensemble (256 runs, 7.09 M cells) in its launch
+    configuration (autotuned tiles, graph-replayed steps): every run ends with
+    a clean status word, and four sampled runs (the smallest, the largest and
+    two drawn ones) equal the oracle within the FP32 budget."""
+    from paper_1903_09043_gb300 import ark
+    from parity import F32_STEP_TOL, field_errors
+    runs = I.ensemble()
+    assert len(runs) == 256
+    sizes = [p.ncells for p, _ in runs]
+    picks = sorted({int(np.argmin(sizes)), int(np.argmax(sizes)), 17, 200})
+    n = 8
+    with ark.Batch([p for p, _ in runs], "f32split", stream=_stream()) as b:
+        for i, (_, U) in enumerate(runs):
+            b.set_state(i, U)
+        b.tune(reps=2)
+        b.step(n)
+        outs = {i: b.get_state(i) for i in picks}
+        diags = [b.diagnostics(i, check=False) for i in range(len(runs))]
+    assert all(d["status"] == 0 and d["step"] == n for d in diags)
+    for i in picks:
+        prob, U = runs[i]
+        ref, _ = O.run(prob, U, n)
+        errs = field_errors(prob, outs[i], ref)
+        assert max(errs) <= n * F32_STEP_TOL, (i, errs)
