@@ -66,6 +66,7 @@ PATHS = {"f32split": ("f32split", "3d"), "f64": ("f64", "3d"), "f32": ("f32", "3
 # A smaller case of the same set-up (state 160 MB FP32 / 320 MB FP64, still larger
 # than L2) used for ncu captures, which replay each launch many times.
 SMALL = dict(WORKLOAD, workload="rayleigh_benard_3d_256x256x128", n=[256, 256, 128])
+SMALL_2D = dict(WORKLOAD_2D, workload="rayleigh_benard_2d_4096x2048", n=[4096, 2048])   # FP32 state 134 MB
 
 
 def make_workload(w=WORKLOAD):
@@ -390,15 +391,14 @@ def main():
     for p in paths:
         if p not in PATHS:
             raise SystemExit(f"unknown path {p}; choose from {', '.join(PATHS)}")
-    if args.workload == "small":
-        paths = [p for p in paths if PATHS[p][1] == "3d"]
+    w2d = SMALL_2D if args.workload == "small" else WORKLOAD_2D
     results = {}
     head = paths[0]
     work2d = None
     for path in paths:
         precision, kind = PATHS[path]
         if kind == "2d" and work2d is None:
-            work2d = make_workload(WORKLOAD_2D)
+            work2d = make_workload(w2d)
         pprob, pU = (prob, U) if kind == "3d" else work2d
         with torch.cuda.stream(stream):
             sampler = ClockSampler(local) if (rank == 0 and path == head) else None
@@ -427,13 +427,13 @@ def main():
                                  "alg_bytes_per_cell": B, "peak_kind": f"{peak_kind} hbm_gbs (burst copy)"},
                          "issue": issue},
             "launch": shape, "final_t": d["t"], "final_dt": d["dt"], "status": d["status"], "clocks": clocks,
-            "workload": (WORKLOAD_2D if kind == "2d" else wl)["workload"],
+            "workload": (w2d if kind == "2d" else wl)["workload"],
         }
     h = results[head]
     line = {"metric": METRIC, "value": h["value"], "unit": UNIT, "n_gpus": world, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": h["ms_per_step"], "higher_is_better": True, "scaling": "weak",
             "vs_baseline": None, "dtype": h["dtype"], "data": "synthetic",
-            "config": dict(WORKLOAD_2D if PATHS[head][1] == "2d" else wl, path=head,
+            "config": dict(w2d if PATHS[head][1] == "2d" else wl, path=head,
                            l2="inputs (0.5-2.7 GB) exceed L2 (129 MB); no flush",
                            parallelism="replicas" if world > 1 else "single GPU"),
             "roofline": h["roofline"], "clocks": h["clocks"], "gpu_launches": args.steps,
