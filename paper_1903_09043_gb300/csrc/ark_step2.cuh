@@ -27,6 +27,8 @@
 // buffer of each suffices.
 #pragma once
 
+#include <type_traits>
+
 #include "ark_step.cuh"
 
 namespace ark {
@@ -136,15 +138,17 @@ __device__ __forceinline__ void step_block2(const StepArgs& a, const int tile, c
     const int nx = S.nx, ny = S.ny, nv = S.nv;
     const long long N = S.N;
 
-    // roles of this column (warp-uniform in y, so whole warps skip what they do not own)
-    const bool rowR1 = D == 2 || (ly >= -1 && ly <= TY);
-    const bool rowT = D == 2 || (ly >= 0 && ly < TY);
+    // roles of this column.  A stage runs on every lane of the rows that need
+    // it (row roles are warp-uniform: R2X = 32 in 3D, one row in 2D), so no
+    // warp diverges on the x halo; the x-halo lanes form values nobody reads,
+    // from their own slots and in-bounds neighbour slots of the shared
+    // arrays.  Only the lane roles that decide a result -- stores, status
+    // words, the wave-rate maximum -- test the column.
+    const bool rowR1 = D == 2 || (ly >= -1 && ly <= TY);       // rows of the R1 cells (tilde states)
+    const bool rowT = D == 2 || (ly >= 0 && ly < TY);          // rows of the output cells
+    const bool rowFy = D == 3 && ly >= -1 && ly < TY;          // own +y face bounds an output cell
+    const bool rowFyR1 = D == 3 && ly <= TY;                   // own +y face bounds an R1 cell
     const bool inR1 = rowR1 && lx >= -1 && lx <= TX;
-    const bool inT = rowT && lx >= 0 && lx < TX;
-    const bool xfR1 = rowR1 && lx <= TX;                       // own +x face bounds an R1 cell
-    const bool yfR1 = D == 3 && ly <= TY && lx >= -1 && lx <= TX; // own +y face bounds an R1 cell
-    const bool xfT = rowT && lx >= -1 && lx < TX;              // own +x face bounds an output cell
-    const bool yfT = D == 3 && ly >= -1 && ly < TY && lx >= 0 && lx < TX;
 
     // time step of this step, formed once and shared
     Real* const sdt = reinterpret_cast<Real*>(red + NT);
@@ -188,7 +192,7 @@ __device__ __forceinline__ void step_block2(const StepArgs& a, const int tile, c
     const bool colin = gx >= 0 && gx < nx && (D == 2 || (gy >= 0 && gy < ny));
     const unsigned plane_cells = D == 3 ? (unsigned)nx * (unsigned)ny : (unsigned)nx;
     const unsigned cidx = D == 3 ? (unsigned)gx + (unsigned)nx * (unsigned)gy : (unsigned)gx;
-    const bool ocol = inT && (x0 + lx) < nx && (D == 2 || (y0 + ly) < ny);
+    const bool ocol = rowT && lx >= 0 && lx < TX && (x0 + lx) < nx && (D == 2 || (y0 + ly) < ny);
     const unsigned oidx = D == 3 ? (unsigned)(x0 + lx) + (unsigned)nx * (unsigned)(y0 + ly) : (unsigned)(x0 + lx);
     const Real* __restrict__ Uin = S.U;
     Real* __restrict__ Uo = static_cast<Real*>(a.Uout);
@@ -244,22 +248,27 @@ __device__ __forceinline__ void step_block2(const StepArgs& a, const int tile, c
     Real smax_t = 0;
     unsigned status = 0u;
 
-    for (int f = z0 - 2; f <= z1 + 1; ++f) {
+    // One plane of the march.  STEADY: every stage of the pipeline is past its
+    // warm-up and f lies inside the box (z0 + 2 <= f <= z1 - 1), so no phase
+    // or range test is needed; the warm-up and drain planes take the general
+    // form.
+    auto plane = [&](const int f, auto steady_c) {
+        constexpr bool STEADY = decltype(steady_c)::value;
         const Real fr = Real(f);
         // base rows of the planes this pass touches (split form)
         Base4 bf0{}, b10{}, b11{}, b20{}, b22{}, b23{}, b32{};
         constexpr int BR = C::BRING;
         if constexpr (SPLIT) {
             bf0 = base4<BR>(bring, 0, f);          // row f:   rho0, p0, T0, H0
-            if (f >= z0) {
+            if (STEADY || f >= z0) {
                 b10 = base4<BR>(bring, 0, f - 1);  // row f-1: rho0, p0, T0, H0
                 b11 = base4<BR>(bring, 1, f - 1);  //          R0F, Q0, DPP, DPM
             } else if (f >= z0 - 1) {
                 b11 = base4<BR>(bring, 1, f - 1);
             }
-            if (f >= z0 + 1) {
+            if (STEADY || f >= z0 + 1) {
                 b22 = base4<BR>(bring, 2, f - 2);  // row f-2: DRP, DRM, DWP, DWM
-                if (f >= z0 + 2) {
+                if (STEADY || f >= z0 + 2) {
                     b20 = base4<BR>(bring, 0, f - 2);
                     b23 = base4<BR>(bring, 3, f - 2);  //      DQ0
                     b32 = base4<BR>(bring, 2, f - 3);  // row f-3: DRP, DRM, DWP, DWM
@@ -272,7 +281,7 @@ __device__ __forceinline__ void step_block2(const StepArgs& a, const int tile, c
         Cell<D, Real> cc;
         Real ccphi = 0;               // potential of the own cell (PHIA)
         {
-            const bool fin = f >= 0 && f < nv;
+            const bool fin = STEADY || (f >= 0 && f < nv);
             if (fin && colin) {
                 Row<Real> w;
                 w.rho0 = SPLIT ? bf0.x : Real(0);
@@ -310,7 +319,7 @@ __device__ __forceinline__ void step_block2(const StepArgs& a, const int tile, c
 
         // own z face (f-1, f)
         Real zfu[3] = {0, 0, 0};
-        if (f >= z0 - 1 && inR1) {
+        if ((STEADY || f >= z0 - 1) && rowR1) {
             // Phi jump across the face: -g dz for uniform g, rounded once from FP64
             zfu[2] = Real(-0.5) * (cp.drho + cc.drho) * (PHIA ? ccphi - cp.phi : Real(a.fdphi));
             acoustic_face<Real>(vt1[V], cc.u[V], cp.dp, cc.dp, cp.z, zc, cp.rz, rzc, cp.rc, rcc,
@@ -321,7 +330,7 @@ __device__ __forceinline__ void step_block2(const StepArgs& a, const int tile, c
         Real tlB[NF + 1];
 #pragma unroll
         for (int k = 0; k <= NF; ++k) tlB[k] = 0;
-        if (f >= z0 && inR1) {
+        if ((STEADY || f >= z0) && rowR1) {
             const int q1 = f - 1;
             const Real usx_m = FF[0 * NT - SX], pix_m = FF[1 * NT - SX];
             Real ell = lam[0] * (fxp[0] - usx_m);
@@ -361,7 +370,7 @@ __device__ __forceinline__ void step_block2(const StepArgs& a, const int tile, c
                 scale_n<NF>(tlB, pre, rL);
             }
             tlB[NF] = L;
-            const bool valid = (x0 + lx) >= 0 && (x0 + lx) < nx && (D == 2 || ((y0 + ly) >= 0 && (y0 + ly) < ny)) &&
+            const bool valid = inR1 && (x0 + lx) >= 0 && (x0 + lx) < nx && (D == 2 || ((y0 + ly) >= 0 && (y0 + ly) < ny)) &&
                                q1 >= 0 && q1 < nv;
             if (valid && !(L > Real(0))) status |= ST_LTILDE;
         }
@@ -382,7 +391,7 @@ __device__ __forceinline__ void step_block2(const StepArgs& a, const int tile, c
                 qt[d] = Real(0.25) * kc.invdx[d];
                 kinv[d] = kc.kappa * kc.invdx[d];
             }
-            if (f >= z0 + 2) {
+            if (STEADY || f >= z0 + 2) {
                 auto face = [&](auto dirc) {
                     constexpr int dir = decltype(dirc)::value;
                     constexpr int sh = dir == 0 ? SX : SY;
@@ -416,12 +425,12 @@ __device__ __forceinline__ void step_block2(const StepArgs& a, const int tile, c
                     }
                     VF[(dir * C::NV + D) * NT] = Real(0.5) * work + (vj[D] - vt2[D]) * kinv[dir];
                 };
-                if (xfT) face(IC<0>{});
+                if (rowT) face(IC<0>{});
                 if constexpr (D == 3) {
-                    if (yfT) face(IC<1>{});
+                    if (rowFy) face(IC<1>{});
                 }
             }
-            if (f >= z0 + 1 && inT) {
+            if ((STEADY || f >= z0 + 1) && rowT) {
                 Real gn[D];                           // d u_q / d z
 #pragma unroll
                 for (int q = 0; q < D; ++q) gn[q] = (vt1[q] - vt2[q]) * kc.invdx[V];
@@ -448,8 +457,8 @@ __device__ __forceinline__ void step_block2(const StepArgs& a, const int tile, c
         Real tfx[NF], tfy[NF];
 #pragma unroll
         for (int k = 0; k < NF; ++k) tfx[k] = tfy[k] = 0;
-        if (f >= z0 + 2) {
-            if (xfT) {
+        if (STEADY || f >= z0 + 2) {
+            if (rowT) {
                 const bool upL = fx2 >= Real(0);
                 Real up[NF];
 #pragma unroll
@@ -459,7 +468,7 @@ __device__ __forceinline__ void step_block2(const StepArgs& a, const int tile, c
                 for (int k = 0; k < NF; ++k) TF[k * NT] = tfx[k];
             }
             if constexpr (D == 3) {
-                if (yfT) {
+                if (rowFy) {
                     const bool upL = fy2 >= Real(0);
                     Real up[NF];
 #pragma unroll
@@ -475,7 +484,7 @@ __device__ __forceinline__ void step_block2(const StepArgs& a, const int tile, c
         const Real us_hi = zfl[0];
 #pragma unroll
         for (int k = 0; k < NF; ++k) zt_hi[k] = 0;
-        if (f >= z0 + 1 && inT) {
+        if ((STEADY || f >= z0 + 1) && rowT) {
             const bool upL = us_hi >= Real(0);
             Real up[NF];
 #pragma unroll
@@ -494,12 +503,12 @@ __device__ __forceinline__ void step_block2(const StepArgs& a, const int tile, c
         // next base row into the ring (read from the next plane on)
         float bnext = 0.f;
         if constexpr (SPLIT) {
-            if (t < BSTRIDE && f + 1 <= nv + 1) bnext = __ldg(Bt + base_index(t, f + 1));
+            if (t < BSTRIDE && (STEADY || f + 1 <= nv + 1)) bnext = __ldg(Bt + base_index(t, f + 1));
         }
         // own +x / +y acoustic faces of plane f
         Real fxc[3] = {0, 0, 0}, fyc[3] = {0, 0, 0};
-        if (f >= z0 - 1 && f <= z1) {
-            if (xfR1) {
+        if (STEADY || (f >= z0 - 1 && f <= z1)) {
+            if (rowR1) {
                 // with a Phi array the in-plane faces carry S = -(rho_L + rho_R)(Phi_R - Phi_L) / 2
                 if constexpr (PHIA)
                     fxc[2] = Real(-0.5) * (cc.rho + X[C::XI_RHO * NT + SX]) * (X[C::XI_PHI * NT + SX] - ccphi);
@@ -511,7 +520,7 @@ __device__ __forceinline__ void step_block2(const StepArgs& a, const int tile, c
                 if constexpr (PHIA) FF[2 * NT] = fxc[2];
             }
             if constexpr (D == 3) {
-                if (yfR1) {
+                if (rowFyR1) {
                     if constexpr (PHIA)
                         fyc[2] = Real(-0.5) * (cc.rho + X[C::XI_RHO * NT + SY]) * (X[C::XI_PHI * NT + SY] - ccphi);
                     acoustic_face<Real>(cc.u[1], X[NT + SY], cc.dp, X[C::XI_DP * NT + SY], zc, X[C::XI_Z * NT + SY], rzc,
@@ -524,7 +533,7 @@ __device__ __forceinline__ void step_block2(const StepArgs& a, const int tile, c
             }
         }
         // exchange for the next plane's H1
-        if (inR1) {
+        if (rowR1) {
 #pragma unroll
             for (int k = 0; k < NF; ++k) TL[k * NT] = tlB[k];
             if constexpr (VISC) {
@@ -539,7 +548,7 @@ __device__ __forceinline__ void step_block2(const StepArgs& a, const int tile, c
         }
 
         // update of plane f-2
-        if (f >= z0 + 2 && inT) {
+        if ((STEADY || f >= z0 + 2) && rowT) {
             const int q = f - 2;
             const Real L = tlA[NF];
             Real nb[NF];
@@ -571,29 +580,31 @@ __device__ __forceinline__ void step_block2(const StepArgs& a, const int tile, c
                 }
                 if constexpr (SPLIT) nb[D + 1] += dt * Real(b23.x);
             }
+            // the wave rate is formed on every lane of the row; only the
+            // output columns store and fold it into the maximum and status
+            Row<Real> w;
+            w.rho0 = SPLIT ? Real(b20.x) : Real(0);
+            w.p0 = SPLIT ? Real(b20.y) : Real(0);
+            w.T0 = SPLIT ? Real(b20.z) : Real(0);
+            w.phi = a.energy_form ? Real(0) : (PHIA ? phi2 : S.phi.at(fr - Real(2)));
+            Real p, rho;
+            const Real sh = wave_rate<D, Real, SPLIT, VISC>(nb, w, S.eos, kc.invdx, kc.mu, kc.kappa, p, rho);
             if (ocol) {
                 const unsigned idx = oidx + plane_cells * (unsigned)q;
 #pragma unroll
                 for (int k = 0; k < NF; ++k) Uo[k * N + idx] = nb[k];
-                Row<Real> w;
-                w.rho0 = SPLIT ? Real(b20.x) : Real(0);
-                w.p0 = SPLIT ? Real(b20.y) : Real(0);
-                w.T0 = SPLIT ? Real(b20.z) : Real(0);
-                w.phi = a.energy_form ? Real(0) : (PHIA ? phi2 : S.phi.at(fr - Real(2)));
-                Real p, rho;
-                const Real sh = wave_rate<D, Real, SPLIT, VISC>(nb, w, S.eos, kc.invdx, kc.mu, kc.kappa, p, rho);
-                if (!(sh <= smax_t)) smax_t = (sh == sh) ? sh : smax_t;
-                if (sh != sh || p != p) status |= ST_NAN;
-                if (!(rho > Real(0)) || !(p > Real(0))) status |= ST_NONPHYS;
             }
+            if (ocol && !(sh <= smax_t)) smax_t = (sh == sh) ? sh : smax_t;
+            if (ocol && (sh != sh || p != p)) status |= ST_NAN;
+            if (ocol && (!(rho > Real(0)) || !(p > Real(0)))) status |= ST_NONPHYS;
         }
         if constexpr (SPLIT) {
-            if (t < BSTRIDE && f + 1 <= nv + 1) bring[((f + 1) & (BR - 1)) * BSTRIDE + t] = bnext;
+            if (t < BSTRIDE && (STEADY || f + 1 <= nv + 1)) bring[((f + 1) & (BR - 1)) * BSTRIDE + t] = bnext;
         }
         __syncthreads();
 
         // ---------------- rotate the column registers ----------------
-        if (f >= z0 + 1) {
+        if (STEADY || f >= z0 + 1) {
 #pragma unroll
             for (int k = 0; k < NF; ++k) zt_lo[k] = zt_hi[k];
             us_lo = us_hi;
@@ -628,6 +639,14 @@ __device__ __forceinline__ void step_block2(const StepArgs& a, const int tile, c
             phi2 = cp.phi;
             cp.phi = ccphi;
         }
+    };
+    // 2D marches its steady planes in the specialised body.  3D keeps the
+    // general body throughout: there the specialised copy needs more than the
+    // 128 registers a 512-thread block allows and spills, which measured
+    // slower than the phase tests it saves.
+    for (int f = z0 - 2; f <= z1 + 1; ++f) {
+        if (DIM == 2 && f >= z0 + 2 && f <= z1 - 1) plane(f, std::true_type{});
+        else plane(f, std::false_type{});
     }
 
     // block max of the wave rate -> one atomic per block
