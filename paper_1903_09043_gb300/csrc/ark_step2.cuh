@@ -282,7 +282,7 @@ __device__ __forceinline__ void step_block2(const StepArgs& a, const int tile, c
         Real ccphi = 0;               // potential of the own cell (PHIA)
         {
             const bool fin = STEADY || (f >= 0 && f < nv);
-            if (fin && colin) {
+            if ((STEADY && D == 3) || (fin && colin)) {   // 3D steady planes: all-interior tiles, no ghost call
                 Row<Real> w;
                 w.rho0 = SPLIT ? bf0.x : Real(0);
                 w.p0 = SPLIT ? bf0.y : Real(0);
@@ -640,12 +640,15 @@ __device__ __forceinline__ void step_block2(const StepArgs& a, const int tile, c
             cp.phi = ccphi;
         }
     };
-    // 2D marches its steady planes in the specialised body.  3D keeps the
-    // general body throughout: there the specialised copy needs more than the
-    // 128 registers a 512-thread block allows and spills, which measured
-    // slower than the phase tests it saves.
+    // Steady planes take the specialised body.  In 3D only tiles whose every
+    // column loads directly do, and their copy carries no out-of-line ghost
+    // call: with the call inside, the copy needs more than the 128 registers
+    // a 512-thread block allows and spills.  The 2D copy keeps the ghost path
+    // for columns across a wall, which measured faster there.
+    bool allin = true;
+    if constexpr (DIM == 3) allin = __syncthreads_and(colin);   // every column of the tile loads directly
     for (int f = z0 - 2; f <= z1 + 1; ++f) {
-        if (DIM == 2 && f >= z0 + 2 && f <= z1 - 1) plane(f, std::true_type{});
+        if (allin && f >= z0 + 2 && f <= z1 - 1) plane(f, std::true_type{});
         else plane(f, std::false_type{});
     }
 
