@@ -425,9 +425,59 @@ __device__ __forceinline__ void step_block2(const StepArgs& a, const int tile, c
                     }
                     VF[(dir * C::NV + D) * NT] = Real(0.5) * work + (vj[D] - vt2[D]) * kinv[dir];
                 };
-                if (rowT) face(IC<0>{});
                 if constexpr (D == 3) {
-                    if (rowFy) face(IC<1>{});
+                    // the own +x face (lane .x) and +y face (lane .y) of plane f-2
+                    // together, one FP32x2 instruction for both: the same
+                    // arithmetic as face() with the roles of x and y swapped.
+                    // Rows -1 .. TY-1 need the y face; the x face of row -1 is
+                    // formed too and never read.
+                    if (rowFy) {
+                        const float2 m1 = pr(-1.f, -1.f);
+                        auto sub = [&](float2 x, float2 y) { return __ffma2_rn(y, m1, x); };   // x - y
+                        auto add = [](float2 x, float2 y) { return __fadd2_rn(x, y); };
+                        auto ld = [&](int ix, int iy) { return pr(VT[ix], VT[iy]); };
+                        const float2 inv = pr(kc.invdx[0], kc.invdx[1]);
+                        const float2 qtt = pr(qt[1], qt[0]);            // tangential scale of each face
+                        const float2 qtv = pr(qt[V], qt[V]);
+                        const float2 mu_2 = pr(mu, mu), mu2_2 = pr(mu2, mu2), eta_2 = pr(eta, eta);
+                        // neighbour values: normal (N), tangential (T), vertical (V) velocity, temperature
+                        const float2 jN = ld(0 * NT + SX, 1 * NT + SY), jT = ld(1 * NT + SX, 0 * NT + SY);
+                        const float2 jV = ld(2 * NT + SX, 2 * NT + SY), jH = ld(3 * NT + SX, 3 * NT + SY);
+                        const float2 oN = pr(vt2[0], vt2[1]), oT = pr(vt2[1], vt2[0]);
+                        const float2 oV = pr(vt2[2], vt2[2]), oH = pr(vt2[3], vt2[3]);
+                        const float2 gN = __fmul2_rn(sub(jN, oN), inv);
+                        const float2 gT = __fmul2_rn(sub(jT, oT), inv);
+                        const float2 gV = __fmul2_rn(sub(jV, oV), inv);
+                        // averaged tangential differences of the normal (dN) and tangential (dT) components
+                        const float2 dN = __fmul2_rn(add(sub(ld(0 * NT + SY, 1 * NT + SX), ld(0 * NT - SY, 1 * NT - SX)),
+                                                         sub(ld(0 * NT + SX + SY, 1 * NT + SY + SX),
+                                                             ld(0 * NT + SX - SY, 1 * NT + SY - SX))),
+                                                     qtt);
+                        const float2 dT = __fmul2_rn(add(sub(ld(1 * NT + SY, 0 * NT + SX), ld(1 * NT - SY, 0 * NT - SX)),
+                                                         sub(ld(1 * NT + SX + SY, 0 * NT + SY + SX),
+                                                             ld(1 * NT + SX - SY, 0 * NT + SY - SX))),
+                                                     qtt);
+                        const float2 zN = __fmul2_rn(add(pr(DZ[0 * NT], DZ[1 * NT]), pr(DZ[0 * NT + SX], DZ[1 * NT + SY])), qtv);
+                        const float2 zV = __fmul2_rn(add(pr(DZ[V * NT], DZ[V * NT]), pr(DZ[V * NT + SX], DZ[V * NT + SY])), qtv);
+                        const float2 tauT = __fmul2_rn(mu_2, add(gT, dN));
+                        const float2 divu = add(add(gN, dT), zV);
+                        const float2 tauV = __fmul2_rn(mu_2, add(gV, zN));
+                        const float2 tauN = __ffma2_rn(eta_2, divu, __fmul2_rn(mu2_2, gN));
+                        float2 work = __fmul2_rn(tauN, add(oN, jN));
+                        work = __ffma2_rn(tauT, add(oT, jT), work);
+                        work = __ffma2_rn(tauV, add(oV, jV), work);
+                        const float2 heat = __ffma2_rn(sub(jH, oH), pr(kinv[0], kinv[1]), __fmul2_rn(pr(0.5f, 0.5f), work));
+                        VF[(0 * C::NV + 0) * NT] = tauN.x;
+                        VF[(0 * C::NV + 1) * NT] = tauT.x;
+                        VF[(0 * C::NV + 2) * NT] = tauV.x;
+                        VF[(0 * C::NV + 3) * NT] = heat.x;
+                        VF[(1 * C::NV + 1) * NT] = tauN.y;
+                        VF[(1 * C::NV + 0) * NT] = tauT.y;
+                        VF[(1 * C::NV + 2) * NT] = tauV.y;
+                        VF[(1 * C::NV + 3) * NT] = heat.y;
+                    }
+                } else {
+                    if (rowT) face(IC<0>{});
                 }
             }
             if ((STEADY || f >= z0 + 1) && rowT) {
@@ -507,7 +557,39 @@ __device__ __forceinline__ void step_block2(const StepArgs& a, const int tile, c
         }
         // own +x / +y acoustic faces of plane f
         Real fxc[3] = {0, 0, 0}, fyc[3] = {0, 0, 0};
-        if (STEADY || (f >= z0 - 1 && f <= z1)) {
+        if constexpr (D == 3 && !PHIA) {
+            // 3D: the +x face (lane .x) and the +y face (lane .y) together in
+            // FP32x2 instructions, the arithmetic of acoustic_face() per lane.
+            // Rows -2 .. TY need the y face; the x face of row -2 is formed too
+            // and never read.
+            if ((STEADY || (f >= z0 - 1 && f <= z1)) && rowFyR1) {
+                const float2 uL = pr(cc.u[0], cc.u[1]), uR = pr(X[0 * NT + SX], X[1 * NT + SY]);
+                const float2 dpL = pr(cc.dp, cc.dp), dpR = pr(X[C::XI_DP * NT + SX], X[C::XI_DP * NT + SY]);
+                const float zRx = X[C::XI_Z * NT + SX], zRy = X[C::XI_Z * NT + SY];
+                const float rzRx = X[C::XI_RZ * NT + SX], rzRy = X[C::XI_RZ * NT + SY];
+                const float2 aa = __fmul2_rn(pr(kc.K, kc.K), pr(pmax(zc, zRx), pmax(zc, zRy)));
+                const float2 ninv2a = __fmul2_rn(pr(-kc.halfInvK, -kc.halfInvK), pr(pmin(rzc, rzRx), pmin(rzc, rzRy)));
+                const float2 half = pr(0.5f, 0.5f), m1 = pr(-1.f, -1.f);
+                const float2 jump = __ffma2_rn(dpL, m1, dpR);                                    // dpR - dpL
+                const float2 us = __ffma2_rn(jump, ninv2a, __fmul2_rn(half, __fadd2_rn(uL, uR)));
+                float2 th = pr(1.f, 1.f);
+                if (a.low_mach) {
+                    th.x = pmin(vabs(us.x) * pmin(rcc, X[C::XI_RC * NT + SX]), 1.f);
+                    th.y = pmin(vabs(us.y) * pmin(rcc, X[C::XI_RC * NT + SY]), 1.f);
+                }
+                const float2 du = __ffma2_rn(uL, m1, uR);                                        // uR - uL
+                const float2 hat = __fmul2_rn(__fmul2_rn(pr(-0.5f, -0.5f), aa), th);
+                const float2 dPi = __ffma2_rn(hat, du, __fmul2_rn(half, __fadd2_rn(dpL, dpR)));
+                fxc[0] = us.x;
+                fxc[1] = dPi.x;
+                fyc[0] = us.y;
+                fyc[1] = dPi.y;
+                FF[0 * NT] = fxc[0];
+                FF[1 * NT] = fxc[1];
+                FF[NFF * NT] = fyc[0];
+                FF[(NFF + 1) * NT] = fyc[1];
+            }
+        } else if (STEADY || (f >= z0 - 1 && f <= z1)) {
             if (rowR1) {
                 // with a Phi array the in-plane faces carry S = -(rho_L + rho_R)(Phi_R - Phi_L) / 2
                 if constexpr (PHIA)
