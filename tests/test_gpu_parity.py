@@ -233,6 +233,30 @@ def test_full_size_3d_rb_sampled(precision):
         assert max(errs) <= tol, (p, errs)
 
 
+@pytest.mark.parametrize("precision", ["f64", "f32split"])
+def test_full_size_2d_rb_sampled(precision):
+    """2D Rayleigh-Benard 8192 x 4096 (the benchmark's 2D layer and launch
+    shape: 124-column tiles, four blocks per SM, steady-plane body): one GPU
+    step, compared with the oracle on sampled 2 x 2 windows, including the
+    walls, the periodic seam and the seams between tiles."""
+    prob, U = I.rayleigh_benard(2, (8192, 4096), m=1.3, chi=1.1, Ra=1.1 * 1707.76, amp=1e-4, seed=2)
+    V, d = gpu_run(prob, U, 1, precision=precision)
+    dt = d["dt"]
+    assert d["status"] == 0
+    assert dt == pytest.approx(O.dt(prob, U), rel=1e-14 if precision == "f64" else 1e-6)
+    rng = np.random.default_rng(1)
+    tol = F64_TOL if precision == "f64" else F32_STEP_TOL
+    fl = floors(prob, U)
+    nx, ny = prob.n[0], prob.n[1]
+    pts = _sample_points(prob, rng, 12) + [(123, 2048), (124, 0), (8191, 4094), (0, 4095), (4095, 2047), (4096, 1)]
+    for p in pts:
+        lo = [min(p[0], nx - 2), min(p[1], ny - 2)]
+        hi = [lo[0] + 2, lo[1] + 2]
+        W = O.step_window(prob, U, dt, lo, hi)
+        errs = field_errors(prob, V[:, lo[1]:hi[1], lo[0]:hi[0]], W, fl)
+        assert max(errs) <= tol, (p, errs)
+
+
 @pytest.mark.parametrize("case", ["2d_periodic_visc", "2d_strat_noslip_visc", "3d_strat_noslip_visc_ragged", "3d_rb",
                                   "2d_rb_chi21", "3d_rb_chi21", "2d_rayleigh_taylor", "3d_many_tiles"])
 @pytest.mark.parametrize("precision", ["f32", "f32split"])
