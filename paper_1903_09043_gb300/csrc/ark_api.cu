@@ -164,11 +164,13 @@ void choose_launch(ark_handle* h, int nsm)
     if (h->kinfo.balanced) {
         // one wave of resident blocks; block b takes units [b W, (b + 1) W) of the
         // tile-major list of (tile, plane) units, as runs of planes per tile.
-        // W >= 16 keeps the pipeline warm-up (4 fronts per run) small.
+        // A grid too small to fill the wave takes runs of at least 4 planes: more
+        // blocks and shorter marches (each run adds 4 planes of pipeline warm-up),
+        // which is what sets the step time when the GPU is not full.
         const long long total = (long long)tiles * nv;
         const long long resident = (long long)nsm * h->kinfo.blocks_per_sm;
         long long W = (total + resident - 1) / resident;
-        if (W < 16) W = 16;
+        if (W < 4) W = 4;
         h->work_per_block = W;
         h->planes = (int)(W < nv ? W : nv);
         h->grid = dim3((unsigned)((total + W - 1) / W), 1, 1);

@@ -47,7 +47,7 @@ struct StepArgs {
     double mu, kappa, K, cfl;
     int low_mach;
     int energy_form;        // 0: rho*calE (Sec. 2); 1: rho E with the (uS) source (Appendix B)
-    long long work_per_block;   // balanced schedule: (tile, plane) units per block (column kernels)
+    long long work_per_block;   // balanced schedule: (tile, plane) units per block (single-grid kernels)
     int bc_lo[3], bc_hi[3];
     double Tw_lo[3], Tw_hi[3];
     int planes;             // planes of the gravity axis per block

@@ -609,12 +609,13 @@ __device__ __noinline__ void slow_cell(const Stepper<DIM, Real, SPLIT, VISC, TX,
     }
 }
 
-// One block's share of a step: in-plane tile `tile`, planes [chunk * planes,
-// (chunk + 1) * planes) of the gravity axis.  Called by the single-grid kernel
-// (one block per (tile, chunk)) and by the batched kernel (work items of many runs).
+// One block's share of a step: in-plane tile `tile`, planes [z0, z1) of the
+// gravity axis; `lead` marks the one share per step that advances the clock.
+// Called by the single-grid kernel (runs of planes of a balanced schedule) and
+// by the batched kernel (work items of many runs).
 template <int DIM, typename Real, bool SPLIT, bool VISC, int TX, int TY, bool PHIA = false>
-__device__ __forceinline__ void step_block(const StepArgs& a, const int tile, const int chunk,
-                                           unsigned char* smem_raw)
+__device__ __forceinline__ void step_block(const StepArgs& a, const int tile, const int z0, const int z1,
+                                           const bool lead, unsigned char* smem_raw)
 {
     using C = StepCfg<DIM, Real, SPLIT, VISC, TX, TY, PHIA>;
     constexpr int D = DIM, NF = DIM + 2, V = DIM - 1;
@@ -627,8 +628,6 @@ __device__ __forceinline__ void step_block(const StepArgs& a, const int tile, co
     const int tid = threadIdx.x;
     const int x0 = (tile % a.tiles_x) * TX;
     const int y0 = D == 3 ? (tile / a.tiles_x) * TY : 0;
-    const int z0 = chunk * a.planes;
-    const int z1 = min(z0 + a.planes, S.nv);
     const int nx = S.nx, ny = S.ny, nv = S.nv;
     const Real* __restrict__ U = S.U;
     const long long N = S.N;
@@ -639,7 +638,7 @@ __device__ __forceinline__ void step_block(const StepArgs& a, const int tile, co
     if (tid == 0) {
         double dt_d = a.dt_fixed;
         if (!(dt_d > 0.0)) dt_d = a.cfl / __longlong_as_double((long long)a.smax[a.slot_read]);
-        if (tile == 0 && chunk == 0) {
+        if (lead) {   // once per step: clear the slot two steps ahead, advance the clock
             a.smax[a.slot_reset] = 0ull;
             *a.time += dt_d;
             *a.dt_last = dt_d;
@@ -1089,13 +1088,29 @@ __device__ __forceinline__ void step_block(const StepArgs& a, const int tile, co
     if (status) atomicOr(a.status, status);
 }
 
-// One launch = one step of one grid: block (x, y) = (in-plane tile, chunk of planes).
+// One launch = one step of one grid.  Balanced schedule: the grid is one wave
+// of resident blocks, and block b marches units [b W, (b + 1) W) of the
+// tile-major list of (tile, plane) units, as one run of planes per tile it
+// touches (W = work_per_block).
 template <int DIM, typename Real, bool SPLIT, bool VISC, int TX, int TY, bool PHIA = false>
 __global__ void __launch_bounds__(TX * TY, sizeof(Real) == 8 ? 1 : 2)
 ark_step_kernel(const __grid_constant__ StepArgs a)
 {
     extern __shared__ __align__(16) unsigned char smem_raw[];
-    step_block<DIM, Real, SPLIT, VISC, TX, TY, PHIA>(a, blockIdx.x, blockIdx.y, smem_raw);
+    const int nv = a.n[DIM - 1];
+    const long long total = (long long)a.tiles_x * a.tiles_y * nv;
+    long long u = (long long)blockIdx.x * a.work_per_block;
+    const long long end = min(u + a.work_per_block, total);
+    bool lead = blockIdx.x == 0;
+    while (u < end) {
+        const int tile = (int)(u / nv);
+        const int z0 = (int)(u - (long long)tile * nv);
+        const int z1 = (int)min((long long)nv, z0 + (end - u));
+        step_block<DIM, Real, SPLIT, VISC, TX, TY, PHIA>(a, tile, z0, z1, lead, smem_raw);
+        u += z1 - z0;
+        lead = false;
+        __syncthreads();   // the next run reuses the shared plane rings
+    }
 }
 
 // Work item of the batched step: one (run, tile, chunk).
@@ -1122,7 +1137,10 @@ ark_batch_kernel(const StepArgs* __restrict__ runs, const BatchItem* __restrict_
         if (it >= nitems) break;
         if (it == 0 && threadIdx.x == 0) ctr[ctr_next] = 0;
         const BatchItem w = items[it];
-        step_block<DIM, Real, SPLIT, VISC, TX, TY>(runs[w.run], w.tile, w.chunk, smem_raw);
+        const StepArgs& r = runs[w.run];
+        const int z0 = w.chunk * r.planes;
+        step_block<DIM, Real, SPLIT, VISC, TX, TY>(r, w.tile, z0, min(z0 + r.planes, r.n[DIM - 1]),
+                                                   w.tile == 0 && w.chunk == 0, smem_raw);
     }
 }
 

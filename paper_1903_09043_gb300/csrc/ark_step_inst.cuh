@@ -39,6 +39,7 @@ StepKernelInfo step_info()
     if (b < 1) b = 1;
     if (b * C::NT > 2048) b = 2048 / C::NT;
     k.blocks_per_sm = b;
+    k.balanced = true;
     return k;
 }
 
