@@ -153,6 +153,15 @@ def test_dt_uniform_state_closed_form():
     pv = prob.replace(mu=10.0, kappa=0.0)
     expect_p = prob.cfl / (2 * (4 * 10.0 / 3.0) * (1 / dx ** 2 + 1 / dy ** 2))
     assert O.dt(pv, U) == pytest.approx(expect_p, rel=1e-14)
+    # ... and a large conductivity to the thermal one, kappa (gamma - 1) / rho (R3),
+    # which wins over the viscous one when it is the larger diffusivity
+    rho = float(U[0].flat[0])
+    assert np.all(U[0] == rho)
+    pk = prob.replace(mu=0.0, kappa=20.0)
+    expect_k = prob.cfl / (2 * (20.0 * 0.4 / rho) * (1 / dx ** 2 + 1 / dy ** 2))
+    assert O.dt(pk, U) == pytest.approx(expect_k, rel=1e-14)
+    pb = prob.replace(mu=1.0, kappa=20.0)
+    assert O.dt(pb, U) == pytest.approx(expect_k, rel=1e-14)
 
 
 # --------------------------------------------------------------------------
