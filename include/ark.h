@@ -147,7 +147,8 @@ typedef struct {
 typedef struct ark_handle ark_handle;
 
 /* Create a solver for one grid.  Validates p (dims, sizes >= 1, n >= 2 along
- * wall/outflow axes, gamma > 1, K >= 1, cfl > 0, mu, kappa >= 0, periodic
+ * wall/outflow axes, finite box corners and gravity, finite gamma > 1,
+ * K >= 1, cfl > 0, mu, kappa >= 0, all finite, periodic
  * axes without gravity; ARK_F32_SPLIT: fixed-temperature walls only at the
  * two ends of the gravity axis and energy_form 0; ARK_F32 and ARK_F32_SPLIT:
  * fewer than 2^32 cells, else ARK_ERR_UNSUPPORTED), allocates the device state (two ping-pong copies of nf * N
@@ -213,20 +214,32 @@ ark_status ark_launch_shape(const ark_handle* h, int* tx, int* ty, int* planes, 
  * when they need a time step (a memory pool or arena that owns the device, a
  * host thread that must not trigger an allocation, which can synchronise the
  * device or fail when memory is full).
- *   p   problem description; p->precision must be ARK_F64 (the state is FP64)
+ *   p   problem description, checked by the rules of ark_create;
+ *       p->precision must be ARK_F64 (the state is FP64)
  *   U   device pointer, nf * N FP64 values in the layout above, read only
  *   dt  device pointer to one double; receives cfl / max wave rate (the
- *       formula at ark_params.cfl), written on `stream`
+ *       formula at ark_params.cfl), written on `stream`.  If any cell has
+ *       rho <= 0, p + p_inf <= 0 or a NaN wave rate, *dt receives NaN
+ *       instead, so a bad state never yields a finite step from its healthy
+ *       cells.
  * Scratch: a fixed array of 16384 doubles (128 KiB) inside the library's
  * device image, held by every GPU that loads the library until the process
  * exits; it bounds N to 67,108,864 cells (4096 cells per scratch slot).
  * Larger grids are rejected with ARK_ERR_INVALID_ARG before any launch.
  * The first call on a device looks up the array's device address
- * (cudaGetSymbolAddress) with that device current; make that first call
- * before any stream capture.  Every call uses the same array and overwrites
- * the slots it reads, so consecutive calls are independent, but calls that
- * overlap on the GPU (unordered streams) race on it.  Calls no allocating
- * routine.  Returns after enqueueing; it does not synchronise. */
+ * (cudaGetSymbolAddress) with that device current and keeps it for the
+ * process; make that first call before any stream capture, and do not use
+ * the call across a cudaDeviceReset (the kept address goes stale).  Every
+ * call uses the same array and overwrites the slots it reads, so consecutive
+ * calls are independent, but calls that overlap on the GPU (unordered
+ * streams) race on it.  Calls no allocating routine.  Returns after
+ * enqueueing; it does not synchronise.
+ * Errors: ARK_ERR_INVALID_ARG (null pointer, parameters outside the rules of
+ * ark_create, a precision other than ARK_F64, too many cells),
+ * ARK_ERR_UNSUPPORTED (p->gravity.phi set: the potential array would need a
+ * device copy), ARK_ERR_CUDA (a launch failed, or an error from the caller's
+ * earlier work was already pending: it is reported, not cleared, and nothing
+ * is launched). */
 ark_status ark_compute_dt_noalloc(const ark_params* p, const double* U, double* dt, void* stream);
 
 /* ---------------------------------------------------------------------------

@@ -81,12 +81,17 @@ namespace {
 using ark::base_args;
 using ark::nv_of;
 
-ark_status validate(const ark_params* p, std::string& msg)
+}  // namespace
+
+ark_status ark::validate_params(const ark_params* p, std::string& msg)
 {
     if (p->grid.dim != 2 && p->grid.dim != 3) { msg = "grid.dim must be 2 or 3"; return ARK_ERR_INVALID_ARG; }
     const int dim = p->grid.dim;
     for (int d = 0; d < dim; ++d) {
         if (p->grid.n[d] < 1) { msg = "grid.n must be >= 1"; return ARK_ERR_INVALID_ARG; }
+        if (!std::isfinite(p->grid.lo[d]) || !std::isfinite(p->grid.hi[d])) {
+            msg = "grid.lo and grid.hi must be finite"; return ARK_ERR_INVALID_ARG;
+        }
         if (!(p->grid.hi[d] > p->grid.lo[d])) { msg = "grid.hi must exceed grid.lo"; return ARK_ERR_INVALID_ARG; }
         for (int s = 0; s < 2; ++s) {
             const int bc = s ? p->bc.hi[d] : p->bc.lo[d];
@@ -102,6 +107,7 @@ ark_status validate(const ark_params* p, std::string& msg)
             msg = "periodic boundaries come in pairs"; return ARK_ERR_INVALID_ARG;
         }
     }
+    if (!std::isfinite(p->gravity.g)) { msg = "gravity.g must be finite"; return ARK_ERR_INVALID_ARG; }
     if (p->bc.lo[dim - 1] == ARK_BC_PERIODIC && p->gravity.g != 0.0) {
         msg = "gravity along a periodic axis"; return ARK_ERR_INVALID_ARG;
     }
@@ -112,14 +118,16 @@ ark_status validate(const ark_params* p, std::string& msg)
             return ARK_ERR_UNSUPPORTED;
         }
     }
-    if (!(p->eos.gamma > 1.0)) { msg = "eos.gamma must be > 1"; return ARK_ERR_INVALID_ARG; }
+    if (!(p->eos.gamma > 1.0) || !std::isfinite(p->eos.gamma)) { msg = "eos.gamma must be finite and > 1"; return ARK_ERR_INVALID_ARG; }
     if (!(p->eos.p_inf >= 0.0) || !std::isfinite(p->eos.p_inf)) {
         msg = "eos.p_inf must be finite and >= 0";
         return ARK_ERR_INVALID_ARG;
     }
-    if (!(p->K >= 1.0)) { msg = "K must be >= 1 (sub-characteristic condition)"; return ARK_ERR_INVALID_ARG; }
-    if (!(p->cfl > 0.0)) { msg = "cfl must be > 0"; return ARK_ERR_INVALID_ARG; }
-    if (!(p->mu >= 0.0) || !(p->kappa >= 0.0)) { msg = "mu and kappa must be >= 0"; return ARK_ERR_INVALID_ARG; }
+    if (!(p->K >= 1.0) || !std::isfinite(p->K)) { msg = "K must be finite and >= 1 (sub-characteristic condition)"; return ARK_ERR_INVALID_ARG; }
+    if (!(p->cfl > 0.0) || !std::isfinite(p->cfl)) { msg = "cfl must be finite and > 0"; return ARK_ERR_INVALID_ARG; }
+    if (!(p->mu >= 0.0) || !(p->kappa >= 0.0) || !std::isfinite(p->mu) || !std::isfinite(p->kappa)) {
+        msg = "mu and kappa must be finite and >= 0"; return ARK_ERR_INVALID_ARG;
+    }
     if (p->precision < ARK_F64 || p->precision > ARK_F32_SPLIT) { msg = "unknown precision"; return ARK_ERR_INVALID_ARG; }
     if (p->low_mach != 0 && p->low_mach != 1) { msg = "low_mach must be 0 or 1"; return ARK_ERR_INVALID_ARG; }
     if (p->energy_form != 0 && p->energy_form != 1) { msg = "energy_form must be 0 or 1"; return ARK_ERR_INVALID_ARG; }
@@ -137,6 +145,8 @@ ark_status validate(const ark_params* p, std::string& msg)
     }
     return ARK_OK;
 }
+
+namespace {
 
 // The FP64 staging buffer of host states for the FP32 forms, allocated once
 // per handle on first use (a per-call allocation of this size returns to the
@@ -225,7 +235,7 @@ ark_status ark_create(const ark_params* p, void* cuda_stream, ark_handle** out)
     if (!p || !out) return ARK_ERR_INVALID_ARG;
     *out = nullptr;
     std::string msg;
-    ark_status st = validate(p, msg);
+    ark_status st = ark::validate_params(p, msg);
     if (st != ARK_OK) return st;
     ark_handle* h = new (std::nothrow) ark_handle();
     if (!h) return ARK_ERR_ALLOC;
@@ -249,6 +259,7 @@ ark_status ark_create(const ark_params* p, void* cuda_stream, ark_handle** out)
     const size_t ctrl_bytes = 64 + 64 + 16 * 8 + (size_t)ark::DIAG_BLOCKS * ark::DG_NTOT * 8;
     if (cudaMalloc(&h->U[0], bytes) != cudaSuccess || cudaMalloc(&h->U[1], bytes) != cudaSuccess ||
         cudaMalloc(&h->ctrl, ctrl_bytes) != cudaSuccess ||
+        cudaMallocHost((void**)&h->status_host, 16) != cudaSuccess ||
         (h->prec == ARK_F32_SPLIT && (cudaMalloc(&h->base, (size_t)ark::BSTRIDE * L * sizeof(float)) != cudaSuccess ||
                                       cudaMalloc((void**)&h->base64, 3 * (size_t)L * sizeof(double)) != cudaSuccess))) {
         cudaGetLastError();
@@ -297,6 +308,7 @@ ark_status ark_destroy(ark_handle* h)
     cudaFree(h->base64);
     cudaFree(h->stage);
     cudaFree(h->phiA);
+    cudaFreeHost(h->status_host);
     delete h;
     return ARK_OK;
 }
@@ -476,23 +488,33 @@ ark_status ark_time(ark_handle* h, double* t, double* dt)
 ark_status ark_sync(ark_handle* h, double timeout_s)
 {
     if (!h) return ARK_ERR_INVALID_ARG;
-    cudaEvent_t ev;
-    ARK_CUDA(h, cudaEventCreateWithFlags(&ev, cudaEventDisableTiming));
-    cudaError_t e = cudaEventRecord(ev, h->stream);
-    if (e != cudaSuccess) { cudaEventDestroy(ev); return cuda_fail(h, e, "cudaEventRecord"); }
     const auto t0 = std::chrono::steady_clock::now();
-    for (;;) {
-        e = cudaEventQuery(ev);
-        if (e == cudaSuccess) break;
-        if (e != cudaErrorNotReady) { cudaEventDestroy(ev); return cuda_fail(h, e, "cudaEventQuery"); }
-        const double el = std::chrono::duration<double>(std::chrono::steady_clock::now() - t0).count();
-        if (el > timeout_s) { cudaEventDestroy(ev); return fail(h, ARK_ERR_TIMEOUT, "stream still busy"); }
-        std::this_thread::sleep_for(std::chrono::microseconds(50));
-    }
-    cudaEventDestroy(ev);
-    unsigned status = 0;
-    ARK_CUDA(h, cudaMemcpy(&status, h->status, sizeof status, cudaMemcpyDeviceToHost));
-    if (status) return fail(h, ARK_ERR_NONPHYSICAL, "device reported a nonphysical state");
+    // wait for everything enqueued on h's stream so far, polling an event
+    // until the time limit
+    auto wait = [&](const char* what) -> ark_status {
+        cudaEvent_t ev;
+        ARK_CUDA(h, cudaEventCreateWithFlags(&ev, cudaEventDisableTiming));
+        cudaError_t e = cudaEventRecord(ev, h->stream);
+        if (e != cudaSuccess) { cudaEventDestroy(ev); return cuda_fail(h, e, "cudaEventRecord"); }
+        for (;;) {
+            e = cudaEventQuery(ev);
+            if (e == cudaSuccess) break;
+            if (e != cudaErrorNotReady) { cudaEventDestroy(ev); return cuda_fail(h, e, "cudaEventQuery"); }
+            const double el = std::chrono::duration<double>(std::chrono::steady_clock::now() - t0).count();
+            if (el > timeout_s) { cudaEventDestroy(ev); return fail(h, ARK_ERR_TIMEOUT, what); }
+            std::this_thread::sleep_for(std::chrono::microseconds(50));
+        }
+        cudaEventDestroy(ev);
+        return ARK_OK;
+    };
+    ark_status st = wait("stream still busy");
+    if (st != ARK_OK) return st;
+    // the status word is read on h's own stream (whose work is done), so other
+    // streams of the device cannot hold the read past the limit
+    ARK_CUDA(h, cudaMemcpyAsync(h->status_host, h->status, sizeof(unsigned), cudaMemcpyDeviceToHost, h->stream));
+    st = wait("status read still pending");
+    if (st != ARK_OK) return st;
+    if (*h->status_host) return fail(h, ARK_ERR_NONPHYSICAL, "device reported a nonphysical state");
     return ARK_OK;
 }
 

@@ -21,6 +21,7 @@ struct ark_handle {
     void* ctrl = nullptr;          // smax[3] | status | pad | time | dt_last | diag out[16] | partials
     unsigned long long* smax = nullptr;
     unsigned int* status = nullptr;
+    unsigned int* status_host = nullptr;   // pinned host copy of the status word (ark_sync)
     double* time = nullptr;
     double* dt_last = nullptr;
     double* diag_out = nullptr;
@@ -39,4 +40,6 @@ namespace ark {
 int nv_of(const ark_handle* h);
 StepArgs base_args(const ark_handle* h);   // every field but Uin/Uout/dt/slots
 ark_status ensure_dt(ark_handle* h);       // wave rate of the current state into slot step % 3
+// The parameter rules of ark_create (include/ark.h); msg receives the reason.
+ark_status validate_params(const ark_params* p, std::string& msg);
 }  // namespace ark

@@ -8,9 +8,12 @@
 // forbids library allocations.  This entry point needs no handle: its only
 // scratch is a fixed array in the library's own device image.
 #include <cmath>
+#include <cstring>
 #include <mutex>
+#include <string>
 
 #include "../../include/ark.h"
+#include "ark_handle.h"
 #include "ark_step.cuh"
 
 namespace {
@@ -22,10 +25,11 @@ constexpr int NA_MAX_BLOCKS = 16384;                                            
 constexpr long long NA_MAX_CELLS = NA_CELLS_PER_BLOCK * NA_MAX_BLOCKS;                   // 67,108,864 cells
 constexpr int NA_MAX_DEVICES = 64;
 
-// One wave-rate maximum per block of the first pass.  Every device that loads
-// the library holds this array until the process exits.  Each call writes the
-// slots it then reads, so nothing needs clearing between calls; two calls that
-// overlap on the GPU (different streams, no ordering) race on it.
+// One wave-rate maximum per block of the first pass (NaN for a block that saw
+// a bad cell).  Every device that loads the library holds this array until the
+// process exits.  Each call writes the slots it then reads, so nothing needs
+// clearing between calls; two calls that overlap on the GPU (different
+// streams, no ordering) race on it.
 static __device__ __align__(256) double ark_noalloc_scratch[NA_MAX_BLOCKS];
 
 std::mutex g_setup_mutex;
@@ -42,6 +46,7 @@ __global__ void __launch_bounds__(NA_THREADS) na_rate_kernel(const __grid_consta
     const double invdx[3] = {1.0 / a.dx[0], 1.0 / a.dx[1], 1.0 / a.dx[2]};
     const long long plane = D == 3 ? (long long)a.n[0] * a.n[1] : (long long)a.n[0];
     double m = 0.0;
+    int bad = 0;   // a cell with rho <= 0, p + p_inf <= 0 or a NaN rate
     for (int k = 0; k < NA_CELLS_PER_THREAD; ++k) {
         const long long idx = blockIdx.x * NA_CELLS_PER_BLOCK + k * NA_THREADS + threadIdx.x;
         if (idx >= a.ncell) break;
@@ -49,17 +54,20 @@ __global__ void __launch_bounds__(NA_THREADS) na_rate_kernel(const __grid_consta
 #pragma unroll
         for (int f = 0; f < D + 2; ++f) b[f] = __ldg(U + f * a.ncell + idx);
         const ark::Row<double> w = ark::row_info<double, false>(a, ph, (int)(idx / plane), nv);
-        double p, rho;
-        const double s = ark::wave_rate<D, double, false, VISC>(b, w, eos, invdx, a.mu, a.kappa, p, rho);
-        if (!(s <= m)) m = (s == s) ? s : m;
+        double pe, rho;
+        const double s = ark::wave_rate<D, double, false, VISC>(b, w, eos, invdx, a.mu, a.kappa, pe, rho);
+        if (!(rho > 0.0) || !(pe > 0.0) || s != s) bad = 1;
+        else if (s > m) m = s;
     }
     red[threadIdx.x] = m;
-    __syncthreads();
+    // one flag for the block: every slot of the first pass is written on every
+    // call, NaN when the block saw a bad cell
+    bad = __syncthreads_or(bad);
     for (int s = NA_THREADS / 2; s > 0; s >>= 1) {
         if (threadIdx.x < s) red[threadIdx.x] = fmax(red[threadIdx.x], red[threadIdx.x + s]);
         __syncthreads();
     }
-    if (threadIdx.x == 0) partial[blockIdx.x] = red[0];
+    if (threadIdx.x == 0) partial[blockIdx.x] = bad ? __longlong_as_double(0x7ff8000000000000ll) : red[0];
 }
 
 __global__ void __launch_bounds__(NA_THREADS) na_final_kernel(const double* partial, int nblocks, double cfl,
@@ -67,17 +75,26 @@ __global__ void __launch_bounds__(NA_THREADS) na_final_kernel(const double* part
 {
     __shared__ double red[NA_THREADS];
     double m = 0.0;
-    for (int i = threadIdx.x; i < nblocks; i += NA_THREADS) m = fmax(m, partial[i]);
+    int bad = 0;
+    for (int i = threadIdx.x; i < nblocks; i += NA_THREADS) {
+        const double v = partial[i];
+        if (v != v) bad = 1;
+        else m = fmax(m, v);
+    }
     red[threadIdx.x] = m;
-    __syncthreads();
+    bad = __syncthreads_or(bad);
     for (int s = NA_THREADS / 2; s > 0; s >>= 1) {
         if (threadIdx.x < s) red[threadIdx.x] = fmax(red[threadIdx.x], red[threadIdx.x + s]);
         __syncthreads();
     }
-    if (threadIdx.x == 0) *dt_out = cfl / red[0];
+    // a bad state yields NaN rather than a finite step from its healthy cells
+    if (threadIdx.x == 0) *dt_out = bad ? __longlong_as_double(0x7ff8000000000000ll) : cfl / red[0];
 }
 
-// Device address of the scratch array on the current device, looked up once.
+// Device address of the scratch array on the current device, looked up once
+// per device ordinal and kept for the life of the process.  A cudaDeviceReset
+// unloads the module and makes the kept address stale, so the entry point
+// must not be used across a reset.
 cudaError_t scratch_for_current_device(double** out)
 {
     int dev = 0;
@@ -100,20 +117,18 @@ cudaError_t scratch_for_current_device(double** out)
 extern "C" ark_status ark_compute_dt_noalloc(const ark_params* p, const double* U, double* dt, void* stream)
 {
     if (!p || !U || !dt) return ARK_ERR_INVALID_ARG;
-    const int dim = p->grid.dim;
-    if (dim != 2 && dim != 3) return ARK_ERR_INVALID_ARG;
+    std::string msg;
+    const ark_status vs = ark::validate_params(p, msg);   // the rules of ark_create
+    if (vs != ARK_OK) return vs;
     if (p->precision != ARK_F64) return ARK_ERR_INVALID_ARG;
     if (p->gravity.phi) return ARK_ERR_UNSUPPORTED;   // the potential array would need a device copy
-    if (!(p->eos.gamma > 1.0) || !(p->eos.p_inf >= 0.0) || !std::isfinite(p->eos.p_inf) || !(p->cfl > 0.0) ||
-        !(p->mu >= 0.0) || !(p->kappa >= 0.0))
-        return ARK_ERR_INVALID_ARG;
+    const int dim = p->grid.dim;
     long long ncell = 1;
     ark::StepArgs a;
     memset(&a, 0, sizeof a);
     a.dim = dim;
     for (int d = 0; d < 3; ++d) {
         if (d < dim) {
-            if (p->grid.n[d] < 1 || !(p->grid.hi[d] > p->grid.lo[d])) return ARK_ERR_INVALID_ARG;
             a.n[d] = p->grid.n[d];
             a.dx[d] = (p->grid.hi[d] - p->grid.lo[d]) / p->grid.n[d];
             ncell *= p->grid.n[d];
@@ -135,6 +150,9 @@ extern "C" ark_status ark_compute_dt_noalloc(const ark_params* p, const double* 
     a.ncell = ncell;
     ark::fill_constants(a);
 
+    // an error already pending from the caller's earlier work is left for the
+    // caller and reported here without launching anything
+    if (cudaPeekAtLastError() != cudaSuccess) return ARK_ERR_CUDA;
     double* scratch = nullptr;
     if (scratch_for_current_device(&scratch) != cudaSuccess) return ARK_ERR_CUDA;
     const int nblocks = (int)((ncell + NA_CELLS_PER_BLOCK - 1) / NA_CELLS_PER_BLOCK);
