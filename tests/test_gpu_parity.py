@@ -127,6 +127,21 @@ def test_config_rayleigh_benard_256x128():
     assert d["t"] == pytest.approx(t, rel=1e-13)
 
 
+def _oracle_all_cores():
+    """Context manager: the oracle on every host core (results do not depend on
+    the thread count; each cell is written by one thread)."""
+    import contextlib
+
+    @contextlib.contextmanager
+    def cm():
+        O.set_threads(os.cpu_count() or 1)
+        try:
+            yield
+        finally:
+            O.set_threads(1)
+    return cm()
+
+
 def _growth_series(prob, U, steps, every, runner):
     ts, vs = [], []
     V = U
@@ -175,6 +190,45 @@ def test_rayleigh_benard_onset_growth_rate_matches_oracle():
     assert rate_ref > 0.0
     assert rate == pytest.approx(rate_ref, rel=1e-5)
     np.testing.assert_allclose(v, v_ref, rtol=1e-6)
+
+
+def test_config_rayleigh_benard_256x128_white_noise_2e4_steps():
+    """The 2D Rayleigh-Benard configuration as stated: 256 x 128, 1.1 Ra_c,
+    every velocity component uniform in (-1e-4, 1e-4) from default_rng(2),
+    2e4 steps with the CFL time step (Sec. 4.5).  The FP64 GPU run equals the
+    oracle: final state within 1e-12 per field, the mean |v| history every
+    1000 steps, and the growth rate fitted to its second half; the FP32-split
+    run gives the same rate."""
+    prob, U = I.rayleigh_benard(2, (256, 128), Ra=1.1 * I.RA_CRITICAL_RIGID, amp=1e-4, seed=2)
+    ark = _ark()
+    clock = [0.0]
+
+    def oracle_runner(V, n):
+        W, t = O.run(prob, V, n)
+        clock[0] += t
+        d = O.diagnostics(prob, W)
+        return W, {"t": clock[0], "mean_abs_v_last": d["mean_abs_v_last"]}
+
+    with _oracle_all_cores():
+        ref, rate_ref, v_ref = _growth_series(prob, U, 20000, 1000, oracle_runner)
+    rates = {}
+    for precision in ("f64", "f32split"):
+        with ark.Solver(prob, precision, stream=_stream()) as s:
+            s.set_state(U)
+
+            def gpu_runner(V, n):
+                s.step(n)
+                return None, s.diagnostics()
+
+            _, rates[precision], v = _growth_series(prob, U, 20000, 1000, gpu_runner)
+            V = s.get_state()
+            t = s.diagnostics()["t"]
+        if precision == "f64":
+            assert max_error(prob, V, ref) <= F64_TOL
+            assert t == pytest.approx(clock[0], rel=1e-12)
+            np.testing.assert_allclose(v, v_ref, rtol=1e-6)
+    assert rates["f64"] == pytest.approx(rate_ref, rel=1e-5)
+    assert rates["f32split"] == pytest.approx(rate_ref, rel=1e-3)
 
 
 def test_rayleigh_benard_growth_rate_rises_with_ra_and_with_theta():
@@ -231,6 +285,39 @@ def test_full_size_3d_rb_sampled(precision):
         sl = (slice(None),) + tuple(slice(lo[d], hi[d]) for d in reversed(range(3)))
         errs = field_errors(prob, V[sl], W, fl)
         assert max(errs) <= tol, (p, errs)
+
+
+_FULL_3D = {}
+
+
+def _full_3d_reference(nsteps):
+    """The benchmark workload and the oracle's state after ``nsteps`` CFL steps
+    (computed once per session, on every host core)."""
+    if nsteps not in _FULL_3D:
+        prob, U = I.rayleigh_benard(3, (512, 512, 256), m=0.1, chi=1.1, Ra=1e7, amp=1e-3, seed=4)
+        with _oracle_all_cores():
+            ref, t, dts = O.run(prob, U, nsteps, return_dt=True)
+        _FULL_3D.clear()
+        _FULL_3D[nsteps] = (prob, U, ref, t, dts)
+    return _FULL_3D[nsteps]
+
+
+@pytest.mark.parametrize("precision", ["f64", "f32split"])
+def test_full_size_3d_rb_five_steps_every_cell(precision):
+    """3D Rayleigh-Benard 512 x 512 x 256 (the benchmark workload, its launch
+    shape): five GPU steps with the CFL time step against five oracle steps,
+    every cell of every field; FP64 within 1e-12, the FP32-split form within
+    five steps' budget."""
+    prob, U, ref, t_ref, dts = _full_3d_reference(5)
+    V, d = gpu_run(prob, U, 5, precision=precision)
+    assert d["status"] == 0
+    errs = field_errors(prob, V, ref)
+    if precision == "f64":
+        assert max(errs) <= F64_TOL, errs
+        assert d["t"] == pytest.approx(t_ref, rel=1e-13)
+    else:
+        assert max(errs) <= 5 * F32_STEP_TOL, errs
+        assert d["t"] == pytest.approx(t_ref, rel=1e-6)
 
 
 @pytest.mark.parametrize("precision", ["f64", "f32split"])
@@ -369,6 +456,41 @@ def test_conservation_at_scale():
     assert abs(d["energy"] - d0["energy"]) <= 1e-13 * d0["energy"]
     for k in ("mom_x", "mom_y", "mom_z"):
         assert abs(d[k] - d0[k]) <= 1e-13
+
+
+DIAG_CASES = {
+    "2d_atmosphere": lambda: I.atmosphere((37, 29), height=3.0, width=2.5),
+    "2d_stiffened_column": lambda: I.atmosphere((9, 40), p_inf=2.5),
+    "2d_periodic_visc": lambda: I.random_periodic(2, (300, 7), seed=4, mu=0.5, kappa=0.2),
+    "3d_rb": lambda: I.rayleigh_benard(3, (40, 36, 24), amp=1e-3),
+    "3d_periodic": lambda: I.random_periodic(3, (17, 9, 13), seed=6, mu=0.3, kappa=0.4),
+    "2d_potential_array": lambda: I.periodic_potential_state(2, (24, 20)),
+}
+
+
+@pytest.mark.parametrize("case", sorted(DIAG_CASES))
+@pytest.mark.parametrize("precision", ["f64", "f32split"])
+def test_diagnostics_match_oracle(case, precision):
+    """ark_diagnostics (device FP64 tree sums) against the oracle's diagnostics,
+    which are pinned to closed forms; after 3 steps, so that the device sums
+    read a state the kernels wrote."""
+    from parity import sound_speed
+    prob, U = DIAG_CASES[case]()
+    if precision == "f32split" and getattr(prob, "phi", None) is not None:
+        pytest.skip("the split form takes uniform gravity only")
+    V, d = gpu_run(prob, U, 3, precision=precision)
+    ref = O.diagnostics(prob, V)
+    tol = 1e-13 if precision == "f64" else 1e-6
+    mscale = ref["mass"] * float(np.max(sound_speed(prob, V)))
+    for k in ("mass", "energy", "kinetic"):
+        assert abs(d[k] - ref[k]) <= tol * max(abs(ref[k]), 1e-300), (k, d[k], ref[k])
+    for k in ("mom_x", "mom_y", "mom_z"):
+        assert abs(d[k] - ref[k]) <= tol * mscale, (k, d[k], ref[k])
+    cmax = float(np.max(sound_speed(prob, V)))
+    for k in ("max_speed", "mean_abs_v_last"):
+        assert abs(d[k] - ref[k]) <= tol * cmax, (k, d[k], ref[k])
+    assert d["min_rho"] == pytest.approx(ref["min_rho"], rel=tol)
+    assert abs(d["min_p"] - ref["min_p"]) <= tol * max(abs(ref["min_p"]), float(np.max(np.abs(V[-1]))))
 
 
 def test_transpose_symmetry_on_gpu():
