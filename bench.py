@@ -10,8 +10,12 @@ kernel over all 64 Mi cells (acoustic faces, tilde states, transport,
 viscous and heat fluxes, next CFL time step).
 
 Paths timed: ``f32split`` (headline: FP32 state and stencil arithmetic, FP64
-base state) and ``f64`` (FP64 throughout).  ``--impl reference`` times the
-FP64 CPU oracle on slabs of the same workload instead.
+base state) and ``f64`` (FP64 throughout) on that workload; ``f32split_2d``
+on the 2D Rayleigh-Benard layer (8192 x 4096); ``gresho_f32split`` and
+``gresho_f64`` on the inviscid Gresho vortex (8192 x 8192, Sec. 4.2), where
+the step does the fewest operations per byte; and the 256-run ensemble.
+``--impl reference`` times the FP64 CPU oracle on slabs of the same workload
+instead.
 
 Output: one JSON line on rank 0.
 """
@@ -59,18 +63,27 @@ ISSUE_PEAK_GWARP = SMS * 4 * SM_GHZ
 WORKLOAD_2D = {"workload": "rayleigh_benard_2d_8192x4096", "dim": 2, "n": [8192, 4096], "box": [2.0, 1.0],
                "polytrope_m": 1.3, "chi": 1.1, "Ra": 1.1 * 1707.76, "Pr": 1.0, "perturbation": 1e-4, "seed": 2,
                "bc": "periodic x; no-slip fixed-T walls y", "low_mach": 1, "cfl": 0.8}
-# path name -> (precision, workload)
+# Roofline line where HBM can bind: the inviscid Gresho vortex of Sec. 4.2
+# (periodic unit square, rho0 = 1, Ma = 1e-2, low-Mach correction on) on
+# 8192 x 8192 cells (FP32 state 1.07 GB, FP64 2.1 GB), 144 flops per cell.
+WORKLOAD_GRESHO = {"workload": "gresho_2d_8192x8192", "dim": 2, "n": [8192, 8192], "box": [1.0, 1.0],
+                   "mach": 1e-2, "bc": "periodic x,y", "inviscid": True, "low_mach": 1, "cfl": 0.8}
+# path name -> (precision, workload kind)
 PATHS = {"f32split": ("f32split", "3d"), "f64": ("f64", "3d"), "f32": ("f32", "3d"),
-         "f32split_2d": ("f32split", "2d")}
+         "f32split_2d": ("f32split", "2d"), "gresho_f32split": ("f32split", "gresho"),
+         "gresho_f64": ("f64", "gresho"), "gresho_f32": ("f32", "gresho")}
 
 # A smaller case of the same set-up (state 160 MB FP32 / 320 MB FP64, still larger
 # than L2) used for ncu captures, which replay each launch many times.
 SMALL = dict(WORKLOAD, workload="rayleigh_benard_3d_256x256x128", n=[256, 256, 128])
 SMALL_2D = dict(WORKLOAD_2D, workload="rayleigh_benard_2d_4096x2048", n=[4096, 2048])   # FP32 state 134 MB
+SMALL_GRESHO = dict(WORKLOAD_GRESHO, workload="gresho_2d_4096x4096", n=[4096, 4096])    # FP32 state 268 MB
 
 
 def make_workload(w=WORKLOAD):
     from paper_1903_09043_gb300 import inputs as I
+    if w["workload"].startswith("gresho"):
+        return I.gresho(w["n"][0], mach=w["mach"], low_mach=w["low_mach"], cfl=w["cfl"])
     return I.rayleigh_benard(w["dim"], tuple(w["n"]), m=w["polytrope_m"], chi=w["chi"], Ra=w["Ra"], Pr=w["Pr"],
                              amp=w["perturbation"], seed=w["seed"], low_mach=w["low_mach"], cfl=w["cfl"])
 
@@ -210,7 +223,36 @@ def cpu_baseline(prob, U, seconds=10.0, single_seconds=4.0):
     return {"value": value, "unit": UNIT, "cores": cores, "kind": "oracle",
             "sample": f"{k} one-step slabs of 512x512x8 cells of the workload (FP64 oracle, OpenMP {cores} threads)",
             "single_thread": {"value": single, "unit": UNIT, "cores": 1,
-                              "sample": f"{k1} one-step slabs of 512x512x8 cells, one thread"}}
+                              "sample": f"{k1} one-step slabs of 512x512x8 cells, one thread"},
+            "configs": cpu_configs(cores)}
+
+
+def cpu_configs(cores, budget=1.0):
+    """The FP64 oracle on the smaller stated configurations, whole-grid CFL
+    steps for about ``budget`` seconds each, on all cores and on one core:
+    the 128 x 128 isothermal atmosphere, the 256 x 128 Rayleigh-Benard layer
+    and the 1024 x 1024 Gresho vortex (Ma = 1e-2)."""
+    import oracle as O
+    from paper_1903_09043_gb300 import inputs as I
+    cases = {"atmosphere_2d_128x128": I.atmosphere((128, 128)),
+             "rayleigh_benard_2d_256x128": I.rayleigh_benard(2, (256, 128)),
+             "gresho_2d_1024x1024": I.gresho(1024, mach=1e-2)}
+    out = {}
+    for name, (prob, U) in cases.items():
+        row = {}
+        for threads in (cores, 1):
+            O.set_threads(threads)
+            V, k = U, 0
+            t0 = time.perf_counter()
+            while k == 0 or time.perf_counter() - t0 < budget:
+                V = O.step(prob, V, O.dt(prob, V))
+                k += 1
+            el = time.perf_counter() - t0
+            row["all_cores" if threads == cores else "one_core"] = {
+                "value": prob.ncells * k / el, "ms_per_step": 1e3 * el / k, "steps": k, "cores": threads}
+        out[name] = row
+    O.set_threads(cores)
+    return out
 
 
 def run_reference(args, world, rank):
@@ -246,7 +288,11 @@ def run_reference(args, world, rank):
     print(json.dumps(line), flush=True)
 
 
-def time_path(prob, U, precision, args, world, stream, sampler=None):
+def time_path(prob, U, precision, args, world, stream, sampler=None, min_sampled_s=1.0, max_blocks=100):
+    """Device time of K back-to-back steps (CUDA events on the launching stream).
+    With a clock sampler the timed block of exactly K steps is repeated until
+    the sampled region lasts ``min_sampled_s`` (a short block holds too few
+    nvidia-smi samples), and the median block is reported."""
     import torch
     from paper_1903_09043_gb300 import ark
     s = ark.Solver(prob, precision, stream=stream.cuda_stream)
@@ -260,18 +306,24 @@ def time_path(prob, U, precision, args, world, stream, sampler=None):
     ev1 = torch.cuda.Event(enable_timing=True)
     if sampler:
         sampler.start()
-    torch.cuda.synchronize()
-    ev0.record(stream)
-    s.step(args.steps)
-    ev1.record(stream)
-    torch.cuda.synchronize()
+    blocks = []
+    t_start = time.perf_counter()
+    while True:
+        torch.cuda.synchronize()
+        ev0.record(stream)
+        s.step(args.steps)
+        ev1.record(stream)
+        torch.cuda.synchronize()
+        blocks.append(ev0.elapsed_time(ev1) / args.steps)
+        if not sampler or len(blocks) >= max_blocks or time.perf_counter() - t_start >= min_sampled_s:
+            break
     clocks = sampler.stop() if sampler else None
-    ms = ev0.elapsed_time(ev1) / args.steps
+    ms = statistics.median(blocks)
     ms_max = barrier_and_max(ms, world)
     d = s.diagnostics(check=False)
     shape = s.launch_shape()
     s.close()
-    return ms, ms_max, d, shape, clocks
+    return ms, ms_max, d, shape, clocks, len(blocks)
 
 
 def e2e_path(prob, U, path, args, stream):
@@ -299,7 +351,10 @@ def e2e_path(prob, U, path, args, stream):
     s.close()
     nbytes = U.nbytes
     return {"value": prob.ncells * args.steps / el, "unit": UNIT,
-            "h2d_bytes_per_step": nbytes / args.steps, "d2h_bytes_per_step": 16 + nbytes / args.steps}
+            "h2d_bytes_per_step": nbytes / args.steps, "d2h_bytes_per_step": 16 + nbytes / args.steps,
+            "steps_per_upload": args.steps,
+            "note": (f"one FP64 state upload, {args.steps} steps each followed by a 16-byte (t, dt) read, "
+                     "one FP64 state download; the rate rises with the steps per upload")}
 
 
 def batch_path(args, stream, hbm):
@@ -350,10 +405,10 @@ def batch_path(args, stream, hbm):
             "one_at_a_time_value": cells / (ms_one * 1e-3), "one_at_a_time_ms_per_step": ms_one,
             "speedup_vs_one_at_a_time": ms_one / ms, "tile": shape, "tuned": {"tx": tx, "planes": planes},
             "launches_per_step": 1, "runs_with_status": bad,
-            "roofline": {"bound": "alu", "achieved": tflops, "peak": ALU_PEAK_TFLOPS["f32"], "unit": "TFLOP/s",
-                         "frac": tflops / ALU_PEAK_TFLOPS["f32"], "alg_flops_per_cell": flops, "traffic": None,
-                         "hbm": {"achieved": achieved, "peak": hbm, "unit": "GB/s", "frac": achieved / hbm,
-                                 "alg_bytes_per_cell": ALG_BYTES[("f32split", 2)]}}}
+            "roofline": {"bound": "hbm", "achieved": achieved, "peak": hbm, "unit": "GB/s", "frac": achieved / hbm,
+                         "alg_bytes_per_cell": ALG_BYTES[("f32split", 2)], "traffic": kernel_traffic("batch"),
+                         "alu": {"achieved": tflops, "peak": ALU_PEAK_TFLOPS["f32"], "unit": "TFLOP/s",
+                                 "frac": tflops / ALU_PEAK_TFLOPS["f32"], "alg_flops_per_cell": flops}}}
 
 
 def main():
@@ -362,7 +417,7 @@ def main():
     ap.add_argument("--steps", type=int, default=200)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
-    ap.add_argument("--paths", default="f32split,f64,f32split_2d",
+    ap.add_argument("--paths", default="f32split,f64,f32split_2d,gresho_f32split,gresho_f64",
                     help="comma list of " + ", ".join(PATHS) + "; the first is the headline")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
@@ -391,18 +446,22 @@ def main():
     for p in paths:
         if p not in PATHS:
             raise SystemExit(f"unknown path {p}; choose from {', '.join(PATHS)}")
-    w2d = SMALL_2D if args.workload == "small" else WORKLOAD_2D
+    small = args.workload == "small"
+    wdefs = {"3d": wl, "2d": SMALL_2D if small else WORKLOAD_2D, "gresho": SMALL_GRESHO if small else WORKLOAD_GRESHO}
+    works = {"3d": (prob, U)}
     results = {}
     head = paths[0]
-    work2d = None
+    timed_blocks = 1
     for path in paths:
         precision, kind = PATHS[path]
-        if kind == "2d" and work2d is None:
-            work2d = make_workload(w2d)
-        pprob, pU = (prob, U) if kind == "3d" else work2d
+        if kind not in works:
+            works[kind] = make_workload(wdefs[kind])
+        pprob, pU = works[kind]
         with torch.cuda.stream(stream):
             sampler = ClockSampler(local) if (rank == 0 and path == head) else None
-            ms, ms_max, d, shape, clocks = time_path(pprob, pU, precision, args, world, stream, sampler)
+            ms, ms_max, d, shape, clocks, nblocks = time_path(pprob, pU, precision, args, world, stream, sampler)
+        if path == head:
+            timed_blocks = nblocks
         cells = pprob.ncells
         B = ALG_BYTES[(precision, pprob.dim)]
         achieved = cells * B / (ms * 1e-3) / 1e9
@@ -420,22 +479,25 @@ def main():
                      "peak_kind": "4 issue slots per SM per clock at the maximum SM clock; instructions per cell from ncu"}
         results[path] = {
             "value": cells * world / (ms_max * 1e-3), "ms_per_step": ms_max, "dtype": dt_kind,
-            "roofline": {"bound": "alu", "achieved": tflops, "peak": alu_peak, "unit": "TFLOP/s",
-                         "frac": tflops / alu_peak, "traffic": traffic, "alg_flops_per_cell": flops,
-                         "peak_kind": f"{dt_kind.upper()} peak from unit counts and the maximum SM clock",
-                         "hbm": {"achieved": achieved, "peak": hbm, "unit": "GB/s", "frac": achieved / hbm,
-                                 "alg_bytes_per_cell": B, "peak_kind": f"{peak_kind} hbm_gbs (burst copy)"},
+            "roofline": {"bound": "hbm", "achieved": achieved, "peak": hbm, "unit": "GB/s", "frac": achieved / hbm,
+                         "traffic": traffic, "alg_bytes_per_cell": B,
+                         "peak_kind": f"{peak_kind} hbm_gbs (burst copy)",
+                         "alu": {"achieved": tflops, "peak": alu_peak, "unit": "TFLOP/s", "frac": tflops / alu_peak,
+                                 "alg_flops_per_cell": flops,
+                                 "peak_kind": f"{dt_kind.upper()} peak from unit counts and the maximum SM clock"},
                          "issue": issue},
             "launch": shape, "final_t": d["t"], "final_dt": d["dt"], "status": d["status"], "clocks": clocks,
-            "workload": (w2d if kind == "2d" else wl)["workload"],
+            "workload": wdefs[kind]["workload"],
         }
     h = results[head]
     line = {"metric": METRIC, "value": h["value"], "unit": UNIT, "n_gpus": world, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": h["ms_per_step"], "higher_is_better": True, "scaling": "weak",
             "vs_baseline": None, "dtype": h["dtype"], "data": "synthetic",
-            "config": dict(w2d if PATHS[head][1] == "2d" else wl, path=head,
+            "config": dict(wdefs[PATHS[head][1]], path=head,
                            l2="inputs (0.5-2.7 GB) exceed L2 (129 MB); no flush",
-                           parallelism="replicas" if world > 1 else "single GPU"),
+                           parallelism="replicas" if world > 1 else "single GPU",
+                           timed_blocks=(f"{timed_blocks} blocks of exactly {args.steps} steps, median reported "
+                                         "(repeated so that the clock sampler sees the timed region)")),
             "roofline": h["roofline"], "clocks": h["clocks"], "gpu_launches": args.steps,
             "paths": {p: {k: v for k, v in r.items() if k != "clocks"} for p, r in results.items()}}
     if not args.no_batch:
@@ -453,7 +515,7 @@ def main():
     if rank == 0 and not args.no_e2e:
         with torch.cuda.stream(stream):
             hprec, hkind = PATHS[head]
-            hprob, hU = (prob, U) if hkind == "3d" else work2d
+            hprob, hU = works[hkind]
             line["e2e"] = e2e_path(hprob, hU, hprec, args, stream)
     if rank == 0 and world == 1 and not args.no_cpu_baseline and args.workload == "full":
         line["cpu_baseline"] = cpu_baseline(prob, U)

@@ -344,6 +344,31 @@ def test_full_size_2d_rb_sampled(precision):
         assert max(errs) <= tol, (p, errs)
 
 
+_GRESHO = {}
+
+
+@pytest.mark.parametrize("precision", ["f64", "f32split"])
+def test_full_size_gresho_8192_two_steps_every_cell(precision):
+    """Inviscid Gresho vortex on 8192 x 8192 (the benchmark's HBM roofline
+    workload, Sec. 4.2, Ma = 1e-2, its launch shape): two GPU steps with the
+    CFL time step against two oracle steps, every cell of every field."""
+    if not _GRESHO:
+        prob, U = I.gresho(8192, mach=1e-2)
+        with _oracle_all_cores():
+            ref, t, dts = O.run(prob, U, 2, return_dt=True)
+        _GRESHO["v"] = (prob, U, ref, t)
+    prob, U, ref, t_ref = _GRESHO["v"]
+    V, d = gpu_run(prob, U, 2, precision=precision)
+    assert d["status"] == 0
+    errs = field_errors(prob, V, ref)
+    if precision == "f64":
+        assert max(errs) <= F64_TOL, errs
+        assert d["t"] == pytest.approx(t_ref, rel=1e-13)
+    else:
+        assert max(errs) <= 2 * F32_STEP_TOL, errs
+        assert d["t"] == pytest.approx(t_ref, rel=1e-6)
+
+
 @pytest.mark.parametrize("case", ["2d_periodic_visc", "2d_strat_noslip_visc", "3d_strat_noslip_visc_ragged", "3d_rb",
                                   "2d_rb_chi21", "3d_rb_chi21", "2d_rayleigh_taylor", "3d_many_tiles"])
 @pytest.mark.parametrize("precision", ["f32", "f32split"])
