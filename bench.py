@@ -255,6 +255,12 @@ def cpu_configs(cores, budget=1.0):
     return out
 
 
+def run_config(workload, world):
+    """The ``config`` object of the result line (the same in both arms)."""
+    return dict(workload, l2="inputs (0.5-2.7 GB) exceed L2 (129 MB); no flush",
+                parallelism="replicas" if world > 1 else "single GPU")
+
+
 def run_reference(args, world, rank):
     if rank != 0:
         return
@@ -282,7 +288,7 @@ def run_reference(args, world, rank):
     line = {"impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": args.gpus,
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * el / args.steps,
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
-            "config": dict(WORKLOAD),
+            "config": run_config(WORKLOAD, world),
             "cpu_baseline": {"value": value, "unit": UNIT, "cores": cores, "kind": "oracle", "sample": sample},
             "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
     print(json.dumps(line), flush=True)
@@ -493,11 +499,10 @@ def main():
     line = {"metric": METRIC, "value": h["value"], "unit": UNIT, "n_gpus": world, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": h["ms_per_step"], "higher_is_better": True, "scaling": "weak",
             "vs_baseline": None, "dtype": h["dtype"], "data": "synthetic",
-            "config": dict(wdefs[PATHS[head][1]], path=head,
-                           l2="inputs (0.5-2.7 GB) exceed L2 (129 MB); no flush",
-                           parallelism="replicas" if world > 1 else "single GPU",
-                           timed_blocks=(f"{timed_blocks} blocks of exactly {args.steps} steps, median reported "
-                                         "(repeated so that the clock sampler sees the timed region)")),
+            "config": run_config(wdefs[PATHS[head][1]], world),
+            "path": head,
+            "timed_blocks": (f"{timed_blocks} blocks of exactly {args.steps} steps, median reported "
+                             "(repeated so that the clock sampler sees the timed region)"),
             "roofline": h["roofline"], "clocks": h["clocks"], "gpu_launches": args.steps,
             "paths": {p: {k: v for k, v in r.items() if k != "clocks"} for p, r in results.items()}}
     if not args.no_batch:
