@@ -97,8 +97,12 @@ typedef struct {
                                   Ghost values wrap across periodic sides and extend
                                   linearly from the two nearest interior cells across
                                   walls and outflow.  The gravity source S then acts
-                                  on every face (Sec. 2.1.2).  ARK_F64 and ARK_F32;
-                                  ARK_F32_SPLIT returns ARK_ERR_UNSUPPORTED.          */
+                                  on every face (Sec. 2.1.2).  ARK_F64 and ARK_F32
+                                  take any array; ARK_F32_SPLIT takes an array that
+                                  depends on the last (gravity) axis only (one base
+                                  row per level, its tables formed in FP64 from the
+                                  array's row values) and returns ARK_ERR_UNSUPPORTED
+                                  for any other.                                       */
 } ark_gravity;
 
 typedef struct {

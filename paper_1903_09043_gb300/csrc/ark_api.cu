@@ -114,8 +114,14 @@ ark_status ark::validate_params(const ark_params* p, std::string& msg)
     if (p->gravity.phi) {
         if (p->gravity.g != 0.0) { msg = "gravity.g must be 0 when gravity.phi is given"; return ARK_ERR_INVALID_ARG; }
         if (p->precision == ARK_F32_SPLIT) {
-            msg = "a potential array needs ARK_F64 or ARK_F32 (the split form's base state needs Phi = Phi(row))";
-            return ARK_ERR_UNSUPPORTED;
+            // the split form's base state is one row per level of the gravity axis
+            long long plane = 1;
+            for (int d = 0; d + 1 < dim; ++d) plane *= p->grid.n[d];
+            std::vector<double> rows;
+            if (!ark::row_potential(p->gravity.phi, plane, p->grid.n[dim - 1], p->bc.lo[dim - 1], p->bc.hi[dim - 1], rows)) {
+                msg = "ARK_F32_SPLIT takes a potential array that depends on the last (gravity) axis only";
+                return ARK_ERR_UNSUPPORTED;
+            }
         }
     }
     if (!(p->eos.gamma > 1.0) || !std::isfinite(p->eos.gamma)) { msg = "eos.gamma must be finite and > 1"; return ARK_ERR_INVALID_ARG; }
@@ -261,7 +267,7 @@ ark_status ark_create(const ark_params* p, void* cuda_stream, ark_handle** out)
         cudaMalloc(&h->ctrl, ctrl_bytes) != cudaSuccess ||
         cudaMallocHost((void**)&h->status_host, 16) != cudaSuccess ||
         (h->prec == ARK_F32_SPLIT && (cudaMalloc(&h->base, (size_t)ark::BSTRIDE * L * sizeof(float)) != cudaSuccess ||
-                                      cudaMalloc((void**)&h->base64, 3 * (size_t)L * sizeof(double)) != cudaSuccess))) {
+                                      cudaMalloc((void**)&h->base64, 4 * (size_t)L * sizeof(double)) != cudaSuccess))) {
         cudaGetLastError();
         ark_destroy(h);
         return ARK_ERR_ALLOC;
@@ -281,6 +287,13 @@ ark_status ark_create(const ark_params* p, void* cuda_stream, ark_handle** out)
         }
         e = cudaMemcpy(h->phiA, src, (size_t)h->N * h->esz, cudaMemcpyHostToDevice);
         if (e != cudaSuccess) { st = cuda_fail(h, e, "potential upload"); ark_destroy(h); return st; }
+        if (h->prec == ARK_F32_SPLIT) {   // FP64 potential of each row (checked separable by validate)
+            const int nv = nv_of(h);
+            ark::row_potential(p->gravity.phi, h->N / nv, nv, p->bc.lo[h->dim - 1], p->bc.hi[h->dim - 1], h->phi_rows);
+            e = cudaMemcpy(h->base64 + 3 * (size_t)L, h->phi_rows.data(), (size_t)L * sizeof(double),
+                           cudaMemcpyHostToDevice);
+            if (e != cudaSuccess) { st = cuda_fail(h, e, "potential rows upload"); ark_destroy(h); return st; }
+        }
         h->p.gravity.phi = nullptr;   // the caller's array is not referenced after ark_create
     }
     char* c = (char*)h->ctrl;
@@ -351,7 +364,8 @@ ark_status ark_set_state(ark_handle* h, const double* U, int on_device)
             const ark_params& p = h->p;
             const int V = h->dim - 1;
             ark::BaseSpec bs{nv, p.grid.lo[V], (p.grid.hi[V] - p.grid.lo[V]) / nv, p.gravity.g, p.eos.gamma, p.kappa,
-                             p.bc.lo[V], p.bc.hi[V], p.bc.T_lo[V], p.bc.T_hi[V], p.eos.p_inf};
+                             p.bc.lo[V], p.bc.hi[V], p.bc.T_lo[V], p.bc.T_hi[V], p.eos.p_inf,
+                             h->phi_rows.empty() ? nullptr : h->phi_rows.data()};
             ark::build_base_tables(bs, rho, pr, b64, tab);
         }
         e = cudaMemcpyAsync(h->base64, b64.data(), b64.size() * sizeof(double), cudaMemcpyHostToDevice, h->stream);

@@ -93,7 +93,9 @@ __global__ void __launch_bounds__(AUX_THREADS) row_means_kernel(const StepArgs a
     __shared__ double sr[AUX_THREADS], sp[AUX_THREADS];
     const int r = blockIdx.x;
     const long long plane = D == 3 ? (long long)a.n[0] * a.n[1] : (long long)a.n[0];
-    const double phi = -(a.g * (a.lo_v + (r + 0.5) * a.dx[D - 1]));
+    // a caller's potential (split form: separable, one value per row) from the
+    // FP64 row table, else the uniform-gravity potential
+    const double phi = a.phiA ? a.base64[3 * (a.n[D - 1] + 4) + r + 2] : -(a.g * (a.lo_v + (r + 0.5) * a.dx[D - 1]));
     double accr = 0.0, accp = 0.0;
     for (long long i = threadIdx.x; i < plane; i += AUX_THREADS) {
         const long long idx = r * plane + i;
@@ -141,7 +143,8 @@ __global__ void __launch_bounds__(AUX_THREADS) diag_kernel(const StepArgs a, con
          idx += (long long)gridDim.x * blockDim.x) {
         const int r = row_of(a, idx);
         double phi = a.energy_form ? 0.0 : -(a.g * (a.lo_v + (r + 0.5) * a.dx[D - 1]));
-        if (a.phiA && !a.energy_form) phi = double(static_cast<const Real*>(a.phiA)[idx]);   // caller's Phi
+        if (a.phiA && !a.energy_form)   // caller's Phi (split form: the FP64 row value)
+            phi = SPLIT ? a.base64[3 * (nv + 4) + r + 2] : double(static_cast<const Real*>(a.phiA)[idx]);
         double rho = double(U[idx]), W = double(U[(D + 1) * a.ncell + idx]);
         if constexpr (SPLIT) {
             rho += a.base64[0 * (nv + 4) + r + 2];

@@ -14,13 +14,16 @@ struct BaseSpec {
     int bc_lo, bc_hi;    // boundary conditions of that axis
     double T_lo, T_hi;   // wall temperatures
     double p_inf;        // stiffened-gas constant (0: ideal gas)
+    const double* phi_rows = nullptr;   // potential of rows -2 .. nv + 1 (nv + 4 values), or
+                                        // nullptr for uniform gravity, Phi = -g x_last
 };
 
 // FP64 base state of F32_SPLIT: rows -2 .. nv + 1 from the interior row means,
 // ghost rows by the boundary rule of the gravity axis applied to the base,
 // then every table entry formed in FP64 and rounded once.  Pressures enter the
 // equation of state as pe = p + p_inf: T0 = pe0 / rho0, the wall balance in pe,
-// and B_P0 holds pe0.
+// and B_P0 holds pe0.  b64 holds four FP64 rows of nv + 4 values: rho0, p0,
+// W0 and the potential Phi of each row.
 inline void build_base_tables(const BaseSpec& s, const std::vector<double>& rho_in, const std::vector<double>& p_in,
                               std::vector<double>& b64, std::vector<float>& tab)
 {
@@ -28,7 +31,7 @@ inline void build_base_tables(const BaseSpec& s, const std::vector<double>& rho_
     const double dv = s.dv;
     const double gm1 = s.gamma - 1.0;
     std::vector<double> rho(L), pr(L), T(L), phi(L);
-    for (int r = -2; r < nv + 2; ++r) phi[r + 2] = -(s.g * (s.lo_v + (r + 0.5) * dv));
+    for (int r = -2; r < nv + 2; ++r) phi[r + 2] = s.phi_rows ? s.phi_rows[r + 2] : -(s.g * (s.lo_v + (r + 0.5) * dv));
     for (int r = 0; r < nv; ++r) {
         rho[r + 2] = rho_in[r];
         pr[r + 2] = p_in[r];
@@ -57,13 +60,14 @@ inline void build_base_tables(const BaseSpec& s, const std::vector<double>& rho_
             }
         }
     }
-    b64.assign(3 * L, 0.0);
+    b64.assign(4 * L, 0.0);
     std::vector<double> W0(L);
     for (int i = 0; i < L; ++i) {
         W0[i] = (pr[i] + s.gamma * s.p_inf) / gm1 + rho[i] * phi[i];
         b64[0 * L + i] = rho[i];
         b64[1 * L + i] = pr[i];
         b64[2 * L + i] = W0[i];
+        b64[3 * L + i] = phi[i];
     }
     std::vector<double> t((size_t)BSTRIDE * L, 0.0);
     auto at = [&](int f, int i) -> double& { return t[(size_t)i * BSTRIDE + f]; };   // i = r + 2
@@ -90,6 +94,33 @@ inline void build_base_tables(const BaseSpec& s, const std::vector<double>& rho_
         at(B_DQ0, i) = s.kappa * ((T[i + 1] - T[i]) - (T[i] - T[i - 1])) / (dv * dv);
     tab.resize(t.size());
     for (size_t i = 0; i < t.size(); ++i) tab[i] = (float)t[i];
+}
+
+// Potential of the rows -2 .. nv + 1 of the gravity (last) axis from a caller's
+// array that depends on that axis only: interior rows from the array, ghost
+// rows by the array's ghost rule along that axis (across a periodic side the
+// row on the other side; across a wall or outflow side the linear extension
+// (1 + L) Phi_0 - L Phi_1 of the boundary row and its inner neighbour, layer
+// L = 1, 2).  Returns false if some cell differs from the first cell of its row.
+inline bool row_potential(const double* phi, long long plane, int nv, int bc_lo, int bc_hi, std::vector<double>& rows)
+{
+    for (int r = 0; r < nv; ++r)
+        for (long long i = 1; i < plane; ++i)
+            if (!(phi[r * plane + i] == phi[r * plane])) return false;
+    rows.assign((size_t)nv + 4, 0.0);
+    for (int r = 0; r < nv; ++r) rows[r + 2] = phi[r * plane];
+    for (int side = 0; side < 2; ++side)
+        for (int layer = 1; layer <= 2; ++layer) {
+            const int g = side == 0 ? -layer : nv - 1 + layer;
+            const int bc = side == 0 ? bc_lo : bc_hi;
+            if (bc == BC_PERIODIC) {
+                rows[g + 2] = rows[((g % nv) + nv) % nv + 2];
+            } else {
+                const int b0 = side == 0 ? 0 : nv - 1, b1 = side == 0 ? 1 : nv - 2;
+                rows[g + 2] = (1.0 + layer) * rows[b0 + 2] - layer * rows[(nv > 1 ? b1 : b0) + 2];
+            }
+        }
+    return true;
 }
 
 }  // namespace ark

@@ -57,7 +57,7 @@ struct StepArgs {
     void* Uout;
     const void* base;       // BaseField tables (F32_SPLIT), else nullptr
     const void* phiA;       // caller-supplied potential at the cell centres (Real, one field), or null
-    const double* base64;   // FP64 rho0, p0, W0 per row, rows -2 .. nv + 1 (F32_SPLIT)
+    const double* base64;   // FP64 rho0, p0, W0, Phi per row, rows -2 .. nv + 1 (F32_SPLIT)
     double dt_fixed;        // > 0: fixed step; otherwise cfl / smax[slot_read]
     unsigned long long* smax;  // 3 slots of FP64 bit patterns (max wave rate)
     int slot_read, slot_write, slot_reset;

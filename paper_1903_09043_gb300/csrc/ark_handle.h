@@ -2,6 +2,7 @@
 #pragma once
 
 #include <string>
+#include <vector>
 
 #include "../../include/ark.h"
 #include "ark_aux.cuh"
@@ -15,9 +16,10 @@ struct ark_handle {
     void* U[2] = {nullptr, nullptr};
     int cur = 0;
     void* base = nullptr;          // Real table [nv + 4][BSTRIDE], row-major
-    double* base64 = nullptr;      // FP64 rho0, p0, W0 [3][nv + 4]
+    double* base64 = nullptr;      // FP64 rho0, p0, W0, Phi [4][nv + 4]
     double* stage = nullptr;       // FP64 staging of host states (FP32 forms), nf * N, made on first use
     void* phiA = nullptr;          // caller-supplied potential, N values of the state precision
+    std::vector<double> phi_rows;  // F32_SPLIT with a potential array: Phi of rows -2 .. nv + 1
     void* ctrl = nullptr;          // smax[3] | status | pad | time | dt_last | diag out[16] | partials
     unsigned long long* smax = nullptr;
     unsigned int* status = nullptr;

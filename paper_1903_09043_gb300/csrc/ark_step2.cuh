@@ -62,7 +62,6 @@ struct Step2Cfg {
     static constexpr size_t O_RED = O_BASE + (SPLIT ? BRING * BSTRIDE * sizeof(float) : 0);
     static constexpr size_t SMEM_BYTES = O_RED + NT * sizeof(double) + 4 * sizeof(double);
     static_assert(NT % 32 == 0 && NT <= 1024, "block must be whole warps");
-    static_assert(!(PHIA && SPLIT), "the split form's base state needs Phi = Phi(row)");
 };
 
 // Four consecutive base-table entries of one row.  The block keeps the rows

@@ -361,6 +361,41 @@ def tilted_atmosphere(n: Sequence[int] = (24, 20), gx: float = -0.3, gy: float =
     return prob, _assemble(prob, rho, [np.zeros((ny, nx)), np.zeros((ny, nx))], p)
 
 
+def row_potential_state(dim: int = 2, n: Sequence[int] = (20, 16), seed: int = 11, amp: float = 1e-2,
+                        mu: float = 0.0, kappa: float = 0.0, low_mach: int = 1, walls: int = NOSLIP_FIXED_T,
+                        g0: float = -2.0, curv: float = 1.5, T0: float = 3.0, beta: float = 1.0,
+                        gamma: float = 5.0 / 3.0, p_inf: float = 0.0) -> Tuple[Problem, np.ndarray]:
+    """Layer under a non-uniform gravity given as a potential array that
+    varies along the last axis only, Phi = -g0 y + curv y^2 (the pull weakens
+    with height), walls at both ends of that axis, periodic across.  The
+    column T = T0 - beta y is the discrete equilibrium of Eq. 18 for that
+    potential; density, pressure and velocity carry a random disturbance of
+    relative size ``amp`` (0: at rest)."""
+    nn = tuple(int(v) for v in n) + (1,) * (3 - len(n))
+    last = dim - 1
+    bc_lo = [PERIODIC] * 3
+    bc_hi = [PERIODIC] * 3
+    bc_lo[last] = walls
+    bc_hi[last] = walls
+    T_lo = [0.0] * 3
+    T_hi = [0.0] * 3
+    T_lo[last] = T0
+    T_hi[last] = T0 - beta
+    prob = Problem(dim=dim, n=nn, lo=(0.0, 0.0, 0.0), hi=(1.0, 1.0, 1.0), gamma=gamma, mu=mu, kappa=kappa,
+                   low_mach=low_mach, bc_lo=tuple(bc_lo), bc_hi=tuple(bc_hi), T_lo=tuple(T_lo), T_hi=tuple(T_hi),
+                   p_inf=p_inf)
+    y = prob.centers(last)
+    prof = -g0 * y + curv * y * y
+    prob = prob.replace(phi=np.ascontiguousarray(_bcast_profile(prob, prof)))
+    T = T0 - beta * y
+    rho, p = hydrostatic_profile(prof, T, T[0] ** 2, p_inf)
+    rng = np.random.default_rng(seed)
+    rhof = _bcast_profile(prob, rho) * (1.0 + amp * rng.uniform(-1, 1, size=prob.shape))
+    pf = _bcast_profile(prob, p) * (1.0 + amp * rng.uniform(-1, 1, size=prob.shape))
+    vel = [amp * rng.uniform(-1, 1, size=prob.shape) for _ in range(dim)]
+    return prob, _assemble(prob, rhof, vel, pf)
+
+
 def periodic_potential_state(dim: int = 2, n: Sequence[int] = (24, 20), seed: int = 7, amp: float = 0.05,
                              A: float = 0.3, mu: float = 0.0, kappa: float = 0.0,
                              low_mach: int = 1) -> Tuple[Problem, np.ndarray]:

@@ -83,3 +83,36 @@ def test_null_arguments(ark):
     assert ark.ark_destroy(None) == ark.ARK_ERR_INVALID_ARG
     assert ark.ark_step(None, 1, -1.0) == ark.ARK_ERR_INVALID_ARG
     assert ark.ark_last_error(None) == b"null handle"
+
+
+def test_split_form_needs_a_row_potential(ark):
+    """A potential array that varies across the planes (tilted gravity) has
+    no one-row-per-level base state: ARK_F32_SPLIT refuses it before any
+    device work; the same array is accepted by the validation of the other
+    forms, and a potential that varies along the gravity axis only passes."""
+    from paper_1903_09043_gb300 import inputs as I
+    prob, _ = I.tilted_atmosphere((16, 12))
+    p = ark.params_from_problem(prob, ark.ARK_F32_SPLIT)
+    h = ark._H()
+    assert ark.ark_create(ctypes.byref(p), None, ctypes.byref(h)) == ark.ARK_ERR_UNSUPPORTED
+    assert not h.value
+    rp, _ = I.row_potential_state(2, (16, 12))
+    q = ark.params_from_problem(rp, ark.ARK_F32_SPLIT)
+    q.K = 0.5      # then rejected for K, after the potential passed
+    assert ark.ark_create(ctypes.byref(q), None, ctypes.byref(h)) == ark.ARK_ERR_INVALID_ARG
+
+
+@pytest.mark.parametrize("field", ["lo", "hi", "g", "mu", "kappa", "cfl", "K", "gamma"])
+def test_non_finite_parameters_rejected(ark, field):
+    p = _params(ark)
+    inf = float("inf")
+    if field in ("lo", "hi"):
+        getattr(p.grid, field)[0] = -inf if field == "lo" else inf
+    elif field == "g":
+        p.gravity.g = float("nan")
+    elif field == "gamma":
+        p.eos.gamma = inf
+    else:
+        setattr(p, field, inf if field != "K" else float("nan"))
+    h = ark._H()
+    assert ark.ark_create(ctypes.byref(p), None, ctypes.byref(h)) == ark.ARK_ERR_INVALID_ARG

@@ -617,13 +617,45 @@ def test_tilted_gravity_atmosphere_stays_at_rest_fp64():
     assert d["status"] == 0
 
 
-@pytest.mark.parametrize("precision", ["f32split"])
-def test_potential_array_unsupported_precisions(precision):
-    ark = _ark()
-    prob, _ = I.tilted_atmosphere((16, 12))
-    with pytest.raises(ark.ArkError) as ei:
-        ark.Solver(prob, precision, stream=_stream())
-    assert ei.value.status == ark.ARK_ERR_UNSUPPORTED
+ROW_POTENTIAL_CASES = {
+    "2d_noslip_visc": lambda: I.row_potential_state(2, (40, 24), mu=0.01, kappa=0.02),
+    "2d_reflect_two_tiles": lambda: I.row_potential_state(2, (300, 12), walls=I.REFLECT_HYDRO),
+    "3d_noslip_visc_multi_tile": lambda: I.row_potential_state(3, (35, 33, 12), mu=0.005, kappa=0.01),
+    "3d_reflect": lambda: I.row_potential_state(3, (19, 6, 16), walls=I.REFLECT_HYDRO),
+    "2d_stiffened": lambda: I.row_potential_state(2, (24, 20), mu=0.01, kappa=0.01, p_inf=3.0),
+}
+
+
+@pytest.mark.parametrize("case", sorted(ROW_POTENTIAL_CASES))
+@pytest.mark.parametrize("precision", ["f32split", "f64"])
+def test_row_potential_matches_oracle(case, precision):
+    """A caller's potential that varies along the gravity axis only (a
+    non-uniform gravity, Sec. 1 takes Phi as any time-independent field): the
+    split form builds its FP64 base tables from the caller's row potential."""
+    prob, U = ROW_POTENTIAL_CASES[case]()
+    n = 20
+    ref, t_ref, dts = O.run(prob, U, n, return_dt=True)
+    V, d = gpu_run(prob, U, n, precision=precision)
+    errs = field_errors(prob, V, ref)
+    assert max(errs) <= (F64_TOL if precision == "f64" else n * F32_STEP_TOL), errs
+    assert d["status"] == 0
+    assert d["dt"] == pytest.approx(dts[-1], rel=1e-13 if precision == "f64" else 1e-5)
+
+
+@pytest.mark.parametrize("dim", [2, 3])
+def test_row_potential_column_at_rest_split(dim):
+    """The discrete equilibrium of Eq. 18 under the non-uniform gravity stays
+    at rest in the split form (its base-state residual formed in FP64), and
+    the plain FP32 form drifts far more."""
+    n = (64, 48) if dim == 2 else (24, 20, 32)
+    prob, U = I.row_potential_state(dim, n, amp=0.0)
+    speed = {}
+    for precision in ("f32split", "f32"):
+        V, d = gpu_run(prob, U, 500, precision=precision)
+        assert d["status"] == 0
+        speed[precision] = d["max_speed"]
+    assert speed["f32split"] < 1e-9
+    assert speed["f32"] > 10 * speed["f32split"]
 
 
 # --------------------------------------------------------------------------

@@ -563,6 +563,17 @@ def test_tilted_gravity_atmosphere_is_a_discrete_equilibrium(low_mach):
     assert O.diagnostics(prob, V)["max_speed"] < 1e-12
 
 
+@pytest.mark.parametrize("walls", [I.NOSLIP_FIXED_T, I.REFLECT_HYDRO])
+def test_non_uniform_gravity_column_is_a_discrete_equilibrium(walls):
+    """A potential that varies along the last axis only, Phi = 2 y + 1.5 y^2
+    (non-uniform gravity), with the column T = 3 - y built by Eq. 18 for it:
+    the state stays at rest, in 2D and 3D, with either wall rule."""
+    for dim, n in ((2, (12, 16)), (3, (6, 5, 16))):
+        prob, U = I.row_potential_state(dim, n, amp=0.0, walls=walls)
+        V, _ = O.run(prob, U, 300)
+        assert O.diagnostics(prob, V)["max_speed"] < 1e-13
+
+
 def test_potential_array_equal_to_uniform_gravity_gives_the_same_steps():
     """Phi given as an array equal to -g y reproduces the uniform-gravity steps
     (to rounding: the wall ghosts of the array extend Phi linearly instead of
