@@ -41,6 +41,7 @@ class _Problem(ctypes.Structure):
         ("energy_form", ctypes.c_int),
         ("phi", ctypes.POINTER(ctypes.c_double)),
         ("p_inf", ctypes.c_double),
+        ("b", ctypes.c_double),
     ]
 
 
@@ -106,6 +107,7 @@ def _struct(prob) -> _Problem:
     s.low_mach = int(prob.low_mach)
     s.energy_form = int(getattr(prob, "energy_form", 0))
     s.p_inf = float(getattr(prob, "p_inf", 0.0))
+    s.b = float(getattr(prob, "b", 0.0))
     phi = getattr(prob, "phi", None)
     if phi is not None:
         arr = np.ascontiguousarray(phi, dtype=np.float64)

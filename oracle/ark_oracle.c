@@ -31,7 +31,8 @@
  *   R1 unsplit multi-D; R2 a = K max(rho_L c_L, rho_R c_R); R3 CFL formula;
  *   R4 dissipative fluxes from U^n in the same update; R5 physical heat-flux
  *   sign; R6 viscous stencil; R7 upwind tie u* >= 0 -> left; R10 wall ghosts;
- *   R11 Phi = -g.x at cell centres; R21 stiffened-gas equation of state.
+ *   R11 Phi = -g.x at cell centres; R21 stiffened-gas equation of state;
+ *   R22 Noble-Abel stiffened gas (covolume b).
  *
  * State layout: nf = dim + 2 fields (rho, m_x, m_y[, m_z], rho*calE), each a
  * block of nx*ny*nz doubles, x fastest.  For dim == 2, nz == 1.
@@ -119,7 +120,12 @@ static double phi_at(const orc_problem* P, const int ijk[3])
  * R21 stiffened gas (Harlow and Amsden 1971; temperature as in Le Metayer,
  * Massoni and Saurel 2004, with (gamma-1) c_v = 1): p = (gamma-1) rho e -
  * gamma p_inf, T = (p + p_inf) / rho, c = sqrt(gamma (p + p_inf) / rho);
- * p_inf = 0 is the ideal gas. */
+ * p_inf = 0 is the ideal gas.
+ * R22 Noble-Abel stiffened gas (Le Metayer and Saurel 2016, without the
+ * reference energy): the covolume b leaves the fraction 1 - b rho of the
+ * volume free, p = (gamma-1) rho e / (1 - b rho) - gamma p_inf,
+ * T = (p + p_inf) (1 - b rho) / rho, c = sqrt(gamma (p + p_inf) / (rho (1 - b rho)));
+ * b = 0 is the stiffened gas (the factor 1 - b rho is then exactly 1). */
 static void to_primitive(const orc_problem* P, cell_t* c)
 {
     double ke = 0.0;
@@ -128,9 +134,10 @@ static void to_primitive(const orc_problem* P, cell_t* c)
         ke += 0.5 * c->rho * c->u[d] * c->u[d];
     }
     double rho_e = c->W - ke - (P->energy_form == 0 ? c->rho * c->phi : 0.0);
-    c->p = (P->gamma - 1.0) * rho_e - P->gamma * P->p_inf;
-    c->T = (c->p + P->p_inf) / c->rho;
-    c->c = sqrt(P->gamma * (c->p + P->p_inf) / c->rho);
+    double free_vol = 1.0 - P->b * c->rho;
+    c->p = (P->gamma - 1.0) * rho_e / free_vol - P->gamma * P->p_inf;
+    c->T = (c->p + P->p_inf) * free_vol / c->rho;
+    c->c = sqrt(P->gamma * (c->p + P->p_inf) / (c->rho * free_vol));
 }
 
 /* Conserved values from (rho, u, p, phi). */
@@ -141,10 +148,12 @@ static void to_conserved(const orc_problem* P, cell_t* c)
         c->m[d] = c->rho * c->u[d];
         ke += 0.5 * c->rho * c->u[d] * c->u[d];
     }
-    /* rho e = (p + gamma p_inf) / (gamma - 1) (R21) */
-    c->W = (c->p + P->gamma * P->p_inf) / (P->gamma - 1.0) + ke + (P->energy_form == 0 ? c->rho * c->phi : 0.0);
-    c->T = (c->p + P->p_inf) / c->rho;
-    c->c = sqrt(P->gamma * (c->p + P->p_inf) / c->rho);
+    /* rho e = (p + gamma p_inf) (1 - b rho) / (gamma - 1) (R21, R22) */
+    double free_vol = 1.0 - P->b * c->rho;
+    c->W = (c->p + P->gamma * P->p_inf) * free_vol / (P->gamma - 1.0) + ke +
+           (P->energy_form == 0 ? c->rho * c->phi : 0.0);
+    c->T = (c->p + P->p_inf) * free_vol / c->rho;
+    c->c = sqrt(P->gamma * (c->p + P->p_inf) / (c->rho * free_vol));
 }
 
 static void load_interior(const orc_problem* P, const double* U, const int ijk[3], cell_t* c)
@@ -175,6 +184,8 @@ static void load_interior(const orc_problem* P, const double* U, const int ijk[3
  * ghost layer 1 for layer 2), with rho_g = (p_g + p_inf) / T_g:
  *   p_g - p_A = -1/2 (rho_A + (p_g + p_inf) / T_g) (Phi_g - Phi_A)
  *   => p_g + p_inf = (p_A + p_inf - 1/2 rho_A dPhi) / (1 + dPhi / (2 T_g)).
+ * With a covolume b (R22) the ghost density is (p_g + p_inf) / (T_g + b (p_g + p_inf))
+ * and the balance is a quadratic in p_g + p_inf.
  * Outflow: zero-gradient copy of (rho, u, p) of the boundary cell.
  */
 static void cell_at(const orc_problem* P, const double* U, const int ijk[3], cell_t* out)
@@ -231,9 +242,19 @@ static void cell_at(const orc_problem* P, const double* U, const int ijk[3], cel
     }
     out->phi = phi_at(P, ijk);
     double dphi = out->phi - A.phi;
-    double pi_g = (A.p + P->p_inf - 0.5 * A.rho * dphi) / (1.0 + dphi / (2.0 * Tg));
+    double pi_g;
+    if (P->b == 0.0) {
+        pi_g = (A.p + P->p_inf - 0.5 * A.rho * dphi) / (1.0 + dphi / (2.0 * Tg));
+    } else {
+        /* R22: rho_g = pi_g / (T_g + b pi_g) turns the balance into
+         * b pi^2 + (T_g - b K + dPhi/2) pi - K T_g = 0, K = pi_A - rho_A dPhi / 2;
+         * its positive root, in the form without cancellation */
+        double K = A.p + P->p_inf - 0.5 * A.rho * dphi;
+        double B = Tg - P->b * K + 0.5 * dphi;
+        pi_g = 2.0 * K * Tg / (B + sqrt(B * B + 4.0 * P->b * K * Tg));
+    }
     out->p = pi_g - P->p_inf;
-    out->rho = pi_g / Tg;
+    out->rho = pi_g / (Tg + P->b * pi_g);
     to_conserved(P, out);
 }
 

@@ -37,6 +37,11 @@ typedef struct {
     double p_inf;       /* stiffened-gas constant of the equation of state,
                            p = (gamma-1) rho e - gamma p_inf, T = (p + p_inf)/rho,
                            c^2 = gamma (p + p_inf)/rho; 0: the ideal gas (R21) */
+    double b;           /* covolume of the Noble-Abel stiffened gas (R22):
+                           p = (gamma-1) rho e / (1 - b rho) - gamma p_inf,
+                           T = (p + p_inf)(1 - b rho)/rho,
+                           c^2 = gamma (p + p_inf)/(rho (1 - b rho));
+                           0: the stiffened gas above */
 } orc_problem;
 
 int orc_nfields(const orc_problem* P);

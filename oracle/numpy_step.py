@@ -11,8 +11,8 @@ ghosts over the x-extended rows, and forms every face and cell quantity as
 array expressions.
 
 What it covers: 2D, uniform gravity along y (Phi = -g y at the centres,
-ghosts included), the stiffened-gas equation of state (p_inf = 0 is the ideal
-gas of Sec. 4), both energy variables (Sec. 2 and Appendix B), every boundary
+ghosts included), the Noble-Abel stiffened-gas equation of state (covolume b
+and p_inf; b = p_inf = 0 is the ideal gas of Sec. 4), both energy variables (Sec. 2 and Appendix B), every boundary
 rule (periodic, reflective hydrostatic wall, no-slip fixed-temperature wall,
 outflow), the low-Mach correction on and off, and the first-order viscous
 and heat fluxes of Sec. 2.2.  The readings of the paper are the same as the C
@@ -34,7 +34,7 @@ def _eos_prims(prob, rho, mx, my, W, phi):
     the stiffened gas of p_inf): u, v, p, T, c."""
     u, v = mx / rho, my / rho
     rho_e = W - 0.5 * rho * (u * u + v * v) - (rho * phi if prob.energy_form == 0 else 0.0)
-    p = (prob.gamma - 1.0) * rho_e - prob.gamma * prob.p_inf
+    p = (prob.gamma - 1.0) * rho_e / (1.0 - prob.b * rho) - prob.gamma * prob.p_inf
     return u, v, p
 
 
@@ -90,7 +90,7 @@ def _fill_axis(prob, Q, phi, axis, rows):
             mirror = G + layer - 1 if side == 0 else G + n - layer
             inner = g + 1 if side == 0 else g - 1                   # neighbour toward the interior
             rho_m, p_m = take("rho", mirror), take("p", mirror)
-            T_m = (p_m + pinf) / rho_m
+            T_m = (p_m + pinf) * (1.0 - prob.b * rho_m) / rho_m
             uu, vv = take("u", mirror), take("v", mirror)
             if bc == REFLECT:
                 Tg = T_m
@@ -99,8 +99,13 @@ def _fill_axis(prob, Q, phi, axis, rows):
                 Tg = 2.0 * Tw - T_m
                 uu, vv = -uu, -vv
             dphi = take("phi", g) - take("phi", inner)
-            qg = (take("p", inner) + pinf - 0.5 * take("rho", inner) * dphi) / (1.0 + dphi / (2.0 * Tg))
-            put("rho", g, qg / Tg)
+            K = take("p", inner) + pinf - 0.5 * take("rho", inner) * dphi
+            if prob.b == 0.0:
+                qg = K / (1.0 + dphi / (2.0 * Tg))
+            else:   # rho_g = q_g / (T_g + b q_g): the balance is a quadratic in q_g
+                Bq = Tg - prob.b * K + 0.5 * dphi
+                qg = 2.0 * K * Tg / (Bq + np.sqrt(Bq * Bq + 4.0 * prob.b * K * Tg))
+            put("rho", g, qg / (Tg + prob.b * qg))
             put("p", g, qg - pinf)
             put("u", g, uu)
             put("v", g, vv)
@@ -113,7 +118,7 @@ def _faces(prob, Q, phi, axis):
     sl_R = (slice(None), slice(1, None)) if axis == 1 else (slice(1, None), slice(None))
     un = Q["u"] if axis == 1 else Q["v"]
     rho, p = Q["rho"], Q["p"]
-    c = np.sqrt(prob.gamma * (p + prob.p_inf) / rho)
+    c = np.sqrt(prob.gamma * (p + prob.p_inf) / (rho * (1.0 - prob.b * rho)))
     a = prob.K * np.maximum(rho[sl_L] * c[sl_L], rho[sl_R] * c[sl_R])
     S = -0.5 * (rho[sl_L] + rho[sl_R]) * (phi[sl_R] - phi[sl_L])
     us = 0.5 * (un[sl_L] + un[sl_R]) - (p[sl_R] - p[sl_L] - S) / (2.0 * a)
@@ -136,7 +141,7 @@ def step(prob, U, dt):
     rho, u, v, p = Q["rho"], Q["u"], Q["v"], Q["p"]
     # conserved values of every padded cell (ghosts from their primitives)
     mx, my = rho * u, rho * v
-    W = (p + prob.gamma * prob.p_inf) / (prob.gamma - 1.0) + 0.5 * rho * (u * u + v * v)
+    W = (p + prob.gamma * prob.p_inf) * (1.0 - prob.b * rho) / (prob.gamma - 1.0) + 0.5 * rho * (u * u + v * v)
     if prob.energy_form == 0:
         W = W + rho * phi
     usx, Pix, Sx = _faces(prob, Q, phi, axis=1)   # (ny+4, nx+3): face between columns i, i+1
@@ -178,7 +183,7 @@ def step(prob, U, dt):
     # first-order dissipative fluxes (Sec. 2.2) from U^n
     if prob.mu != 0.0 or prob.kappa != 0.0:
         mu, eta = prob.mu, -2.0 / 3.0 * prob.mu
-        T = (p + prob.p_inf) / rho
+        T = (p + prob.p_inf) * (1.0 - prob.b * rho) / rho
         for axis in (1, 0):
             dn, dt_ = (dx, dy) if axis == 1 else (dy, dx)
             # normal (n) and tangential (t) velocity components for this face direction

@@ -54,6 +54,9 @@ class Problem:
     phi: np.ndarray | None = dataclasses.field(default=None, compare=False, repr=False)
     # stiffened-gas constant: p = (gamma - 1) rho e - gamma p_inf, T = (p + p_inf) / rho; 0: ideal gas
     p_inf: float = 0.0
+    # covolume of the Noble-Abel stiffened gas: p = (gamma - 1) rho e / (1 - b rho) - gamma p_inf,
+    # T = (p + p_inf)(1 - b rho) / rho; 0: the stiffened gas
+    b: float = 0.0
 
     @property
     def nfields(self) -> int:
@@ -105,7 +108,7 @@ def _assemble(prob: Problem, rho: np.ndarray, vel: Sequence[np.ndarray], p: np.n
     for d in range(prob.dim):
         U[1 + d] = rho * vel[d]
         ke += 0.5 * rho * vel[d] * vel[d]
-    rho_e = (p + prob.gamma * prob.p_inf) / (prob.gamma - 1.0)
+    rho_e = (p + prob.gamma * prob.p_inf) * (1.0 - prob.b * rho) / (prob.gamma - 1.0)
     U[prob.dim + 1] = rho_e + ke + (rho * phi if prob.energy_form == 0 else 0.0)
     return U
 
@@ -116,18 +119,26 @@ def _last_axis_centers(prob: Problem) -> np.ndarray:
 
 
 def hydrostatic_profile(phi: np.ndarray, T: np.ndarray, p0: float,
-                        p_inf: float = 0.0) -> Tuple[np.ndarray, np.ndarray]:
+                        p_inf: float = 0.0, b: float = 0.0) -> Tuple[np.ndarray, np.ndarray]:
     """Discrete hydrostatic column (Eq. 18) from the bottom cell upward, with
-    rho = (p + p_inf) / T (p_inf = 0: the ideal gas)."""
+    rho = (p + p_inf) / T (p_inf = 0: the ideal gas), or with a covolume b,
+    rho = (p + p_inf) / (T + b (p + p_inf)); then each step solves the
+    quadratic b q^2 + (T - b K + dPhi / 2) q - K T = 0 for q = p + p_inf,
+    K = q_below - rho_below dPhi / 2 (its positive root)."""
     n = len(phi)
     q = np.empty(n)    # p + p_inf
     rho = np.empty(n)
     q[0] = p0 + p_inf
-    rho[0] = q[0] / T[0]
+    rho[0] = q[0] / (T[0] + b * q[0])
     for j in range(n - 1):
         dphi = phi[j + 1] - phi[j]
-        q[j + 1] = (q[j] - 0.5 * rho[j] * dphi) / (1.0 + dphi / (2.0 * T[j + 1]))
-        rho[j + 1] = q[j + 1] / T[j + 1]
+        if b == 0.0:
+            q[j + 1] = (q[j] - 0.5 * rho[j] * dphi) / (1.0 + dphi / (2.0 * T[j + 1]))
+        else:
+            K = q[j] - 0.5 * rho[j] * dphi
+            B = T[j + 1] - b * K + 0.5 * dphi
+            q[j + 1] = 2.0 * K * T[j + 1] / (B + math.sqrt(B * B + 4.0 * b * K * T[j + 1]))
+        rho[j + 1] = q[j + 1] / (T[j + 1] + b * q[j + 1])
     return rho, q - p_inf
 
 
@@ -152,18 +163,18 @@ def _bcast_profile(prob: Problem, prof: np.ndarray) -> np.ndarray:
 # ---------------------------------------------------------------------------
 def atmosphere(n: Sequence[int] = (128, 128), height: float = 1.0, width: float = 1.0,
                low_mach: int = 1, gamma: float = 5.0 / 3.0, cfl: float = 0.8,
-               p_inf: float = 0.0) -> Tuple[Problem, np.ndarray]:
+               p_inf: float = 0.0, b: float = 0.0) -> Tuple[Problem, np.ndarray]:
     """Isothermal atmosphere at rest, p = rho = exp(-y), T = 1, g = -1 (Sec. 4.3).
 
     2D, periodic in x, reflective hydrostatic walls in y.  With ``p_inf`` > 0
     the fluid is a stiffened gas (a liquid-like column, rho = (p + p_inf) / T)
     built by the same discrete balance from p = exp(-y) in the bottom cell."""
     prob = Problem(dim=2, n=(n[0], n[1], 1), lo=(0.0, 0.0, 0.0), hi=(width, height, 1.0),
-                   gamma=gamma, g=-1.0, low_mach=low_mach, cfl=cfl, p_inf=p_inf,
+                   gamma=gamma, g=-1.0, low_mach=low_mach, cfl=cfl, p_inf=p_inf, b=b,
                    bc_lo=(PERIODIC, REFLECT_HYDRO, PERIODIC), bc_hi=(PERIODIC, REFLECT_HYDRO, PERIODIC))
     y = prob.centers(1)
     phi = -prob.g * y
-    rho, p = hydrostatic_profile(phi, np.ones_like(y), math.exp(-y[0]), p_inf)
+    rho, p = hydrostatic_profile(phi, np.ones_like(y), math.exp(-y[0]), p_inf, b)
     zero = np.zeros(prob.shape)
     return prob, _assemble(prob, _bcast_profile(prob, rho), [zero, zero], _bcast_profile(prob, p))
 
@@ -275,11 +286,11 @@ def gresho_velocity(prob: Problem) -> Tuple[np.ndarray, np.ndarray]:
 
 def sod(n: int = 100, gamma: float = 1.4, low_mach: int = 1, axis: int = 0,
         cfl: float = 0.8, left: Tuple[float, float] = (1.0, 1.0), right: Tuple[float, float] = (0.125, 0.1),
-        p_inf: float = 0.0) -> Tuple[Problem, np.ndarray]:
+        p_inf: float = 0.0, b: float = 0.0) -> Tuple[Problem, np.ndarray]:
     """Sod shock tube (Sec. 4.1) on [0, 1] along ``axis`` (0 = x, 1 = y) of a 2D
     grid that is one cell wide and periodic across; zero-gradient ends.
     ``left`` / ``right``: (rho, p) of the two states at rest (Sod's by default);
-    ``p_inf`` > 0 makes it a stiffened-gas shock tube."""
+    ``p_inf`` > 0 makes it a stiffened-gas shock tube, ``b`` > 0 a Noble-Abel one."""
     if axis == 0:
         nn, hi = (n, 1, 1), (1.0, 1.0 / n, 1.0)
         bc_lo, bc_hi = (OUTFLOW, PERIODIC, PERIODIC), (OUTFLOW, PERIODIC, PERIODIC)
@@ -287,7 +298,7 @@ def sod(n: int = 100, gamma: float = 1.4, low_mach: int = 1, axis: int = 0,
         nn, hi = (1, n, 1), (1.0 / n, 1.0, 1.0)
         bc_lo, bc_hi = (PERIODIC, OUTFLOW, PERIODIC), (PERIODIC, OUTFLOW, PERIODIC)
     prob = Problem(dim=2, n=nn, lo=(0.0, 0.0, 0.0), hi=hi, gamma=gamma, low_mach=low_mach, cfl=cfl,
-                   bc_lo=bc_lo, bc_hi=bc_hi, p_inf=p_inf)
+                   bc_lo=bc_lo, bc_hi=bc_hi, p_inf=p_inf, b=b)
     x = prob.centers(axis)
     is_left = x < 0.5
     rho = np.where(is_left, left[0], right[0])
@@ -364,7 +375,7 @@ def tilted_atmosphere(n: Sequence[int] = (24, 20), gx: float = -0.3, gy: float =
 def row_potential_state(dim: int = 2, n: Sequence[int] = (20, 16), seed: int = 11, amp: float = 1e-2,
                         mu: float = 0.0, kappa: float = 0.0, low_mach: int = 1, walls: int = NOSLIP_FIXED_T,
                         g0: float = -2.0, curv: float = 1.5, T0: float = 3.0, beta: float = 1.0,
-                        gamma: float = 5.0 / 3.0, p_inf: float = 0.0) -> Tuple[Problem, np.ndarray]:
+                        gamma: float = 5.0 / 3.0, p_inf: float = 0.0, b: float = 0.0) -> Tuple[Problem, np.ndarray]:
     """Layer under a non-uniform gravity given as a potential array that
     varies along the last axis only, Phi = -g0 y + curv y^2 (the pull weakens
     with height), walls at both ends of that axis, periodic across.  The
@@ -383,12 +394,12 @@ def row_potential_state(dim: int = 2, n: Sequence[int] = (20, 16), seed: int = 1
     T_hi[last] = T0 - beta
     prob = Problem(dim=dim, n=nn, lo=(0.0, 0.0, 0.0), hi=(1.0, 1.0, 1.0), gamma=gamma, mu=mu, kappa=kappa,
                    low_mach=low_mach, bc_lo=tuple(bc_lo), bc_hi=tuple(bc_hi), T_lo=tuple(T_lo), T_hi=tuple(T_hi),
-                   p_inf=p_inf)
+                   p_inf=p_inf, b=b)
     y = prob.centers(last)
     prof = -g0 * y + curv * y * y
     prob = prob.replace(phi=np.ascontiguousarray(_bcast_profile(prob, prof)))
     T = T0 - beta * y
-    rho, p = hydrostatic_profile(prof, T, T[0] ** 2, p_inf)
+    rho, p = hydrostatic_profile(prof, T, T[0] ** 2, p_inf, b)
     rng = np.random.default_rng(seed)
     rhof = _bcast_profile(prob, rho) * (1.0 + amp * rng.uniform(-1, 1, size=prob.shape))
     pf = _bcast_profile(prob, p) * (1.0 + amp * rng.uniform(-1, 1, size=prob.shape))
@@ -452,10 +463,11 @@ def random_periodic(dim: int = 2, n: Sequence[int] = (24, 20), seed: int = 0, am
 def stratified_random(dim: int = 2, n: Sequence[int] = (20, 16), seed: int = 1, amp: float = 1e-2,
                       mu: float = 0.0, kappa: float = 0.0, low_mach: int = 1, walls: int = NOSLIP_FIXED_T,
                       chi: float = 3.0, m: float = 1.0, gamma: float = 5.0 / 3.0,
-                      cfl: float = 0.8, p_inf: float = 0.0) -> Tuple[Problem, np.ndarray]:
+                      cfl: float = 0.8, p_inf: float = 0.0, b: float = 0.0) -> Tuple[Problem, np.ndarray]:
     """Polytropic layer with gravity along the last axis, walls at both ends of it,
     periodic across, and a random velocity and pressure disturbance.  With
-    ``p_inf`` > 0 the fluid is a stiffened gas, rho = (p + p_inf) / T."""
+    ``p_inf`` > 0 the fluid is a stiffened gas, rho = (p + p_inf) / T; with a
+    covolume ``b`` a Noble-Abel stiffened gas, rho = (p + p_inf) / (T + b (p + p_inf))."""
     z0 = polytrope_base(chi, m)
     g = -(m + 1.0)
     nn = tuple(n) + (1,) * (3 - len(n))
@@ -471,10 +483,10 @@ def stratified_random(dim: int = 2, n: Sequence[int] = (20, 16), seed: int = 1, 
     hi = [1.0, 1.0, 1.0]
     prob = Problem(dim=dim, n=nn, lo=(0.0, 0.0, 0.0), hi=tuple(hi), gamma=gamma, g=g, mu=mu, kappa=kappa,
                    low_mach=low_mach, cfl=cfl, bc_lo=tuple(bc_lo), bc_hi=tuple(bc_hi), T_lo=tuple(T_lo),
-                   T_hi=tuple(T_hi), p_inf=p_inf)
+                   T_hi=tuple(T_hi), p_inf=p_inf, b=b)
     y = prob.centers(last)
     T = z0 + 1.0 - y
-    rho, p = hydrostatic_profile(-g * y, T, T[0] ** (m + 1.0), p_inf)
+    rho, p = hydrostatic_profile(-g * y, T, T[0] ** (m + 1.0), p_inf, b)
     rng = np.random.default_rng(seed)
     rhof = _bcast_profile(prob, rho) * (1.0 + amp * rng.uniform(-1, 1, size=prob.shape))
     pf = _bcast_profile(prob, p) * (1.0 + amp * rng.uniform(-1, 1, size=prob.shape))

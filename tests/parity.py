@@ -26,8 +26,9 @@ def sound_speed(prob, U):
     if getattr(prob, "energy_form", 0) == 1:
         phi = 0.0 * phi   # rho E holds no potential energy (Appendix B)
     p_inf = getattr(prob, "p_inf", 0.0)
-    p = (prob.gamma - 1.0) * (U[dim + 1] - ke - rho * phi) - prob.gamma * p_inf
-    return np.sqrt(prob.gamma * np.abs(p + p_inf) / rho)
+    free = 1.0 - getattr(prob, "b", 0.0) * rho
+    p = (prob.gamma - 1.0) * (U[dim + 1] - ke - rho * phi) / free - prob.gamma * p_inf
+    return np.sqrt(prob.gamma * np.abs(p + p_inf) / (rho * free))
 
 
 def floors(prob, U):

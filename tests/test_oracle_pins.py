@@ -740,3 +740,109 @@ def test_stiffened_gas_zero_constant_is_the_ideal_gas_bitwise():
     a = O.step(prob, U, 1e-3)
     b = O.step(prob.replace(p_inf=-0.0), U, 1e-3)
     assert np.array_equal(a, b)
+
+
+# --------------------------------------------------------------------------
+# Noble-Abel stiffened gas (covolume b; R22): p = (gamma-1) rho e / (1 - b rho)
+# - gamma p_inf, T = (p + p_inf)(1 - b rho)/rho, c^2 = gamma (p + p_inf)/(rho (1 - b rho))
+# --------------------------------------------------------------------------
+def test_noble_abel_shock_tube_converges_to_exact_riemann_solution():
+    """Shock tube of a Noble-Abel stiffened gas (gamma = 1.4, p_inf = 0.3,
+    b = 0.4: the left state fills 40 % of its volume with covolume) against
+    the exact solution (the covolume gas of Toro, Ch. 4.7, in p + p_inf):
+    density L1 error falls with the grid, pressure and velocity follow the
+    exact profiles.  The waves' positions depend on the sound speed
+    c^2 = gamma (p + p_inf) / (rho (1 - b rho)) and the star state on the
+    energy law, so a law without the covolume fails."""
+    from riemann_exact import sample_covolume
+    g, pinf, b = 1.4, 0.3, 0.4
+    L, R = (1.0, 1.0), (0.125, 0.1)
+    t_end = 0.1
+    e = []
+    for n in (100, 200, 400):
+        prob, U = I.sod(n, gamma=g, p_inf=pinf, b=b, left=L, right=R)
+        V, t = O.run(prob, U, 10 ** 6, t_end=t_end)
+        assert t == pytest.approx(t_end)
+        ex = sample_covolume(prob.centers(0), t_end, 0.5, (L[0], 0.0, L[1]), (R[0], 0.0, R[1]), g, pinf, b)
+        e.append(np.mean(np.abs(V[0, 0] - ex[0])))
+        if n == 400:
+            rho = V[0, 0]
+            u = V[1, 0] / rho
+            p = (g - 1.0) * (V[3, 0] - 0.5 * rho * u * u) / (1.0 - b * rho) - g * pinf
+            assert np.mean(np.abs(p - ex[2])) < 0.01 * L[1]
+            assert np.mean(np.abs(u - ex[1])) < 0.05 * np.max(np.abs(ex[1]))
+    assert e[0] < 0.02
+    assert e[0] > e[1] > e[2]
+    assert math.log2(e[0] / e[2]) / 2 > 0.5
+    # the same tube read with the stiffened-gas law (no covolume) is far off
+    prob, U = I.sod(400, gamma=g, p_inf=pinf, b=b, left=L, right=R)
+    V, _ = O.run(prob.replace(b=0.0), U, 10 ** 6, t_end=t_end)
+    ex = sample_covolume(prob.centers(0), t_end, 0.5, (L[0], 0.0, L[1]), (R[0], 0.0, R[1]), g, pinf, b)
+    assert np.mean(np.abs(V[0, 0] - ex[0])) > 3 * e[2]
+
+
+@pytest.mark.parametrize("low_mach", [0, 1])
+def test_noble_abel_columns_stay_at_rest(low_mach):
+    """Columns of a Noble-Abel stiffened gas built by the discrete balance of
+    Eq. 18 with rho = (p + p_inf) / (T + b (p + p_inf)) are discrete
+    equilibria: an isothermal column between reflective hydrostatic walls
+    (2D) and a viscous polytrope between them (3D), and a conducting, viscous
+    polytrope (linear T) between fixed-temperature no-slip walls, whose heat
+    flux is uniform only if T is the law's temperature.  Mass and energy are
+    conserved."""
+    cases = [I.atmosphere((16, 48), low_mach=low_mach, p_inf=0.5, b=0.3),
+             I.stratified_random(2, (12, 40), amp=0.0, mu=0.02, kappa=0.05, low_mach=low_mach, p_inf=0.2, b=0.2),
+             # reflective walls are adiabatic: viscous, but not conducting, to stay at rest
+             I.stratified_random(3, (5, 4, 24), amp=0.0, mu=0.02, kappa=0.0, low_mach=low_mach, b=0.25,
+                                 walls=I.REFLECT_HYDRO)]
+    for prob, U in cases:
+        assert np.max(prob.b * U[0]) > 0.05      # the covolume matters
+        d0 = O.diagnostics(prob, U)
+        V, _ = O.run(prob, U, 500)
+        d = O.diagnostics(prob, V)
+        assert d["max_speed"] < 1e-12, d["max_speed"]
+        assert abs(d["mass"] - d0["mass"]) <= 1e-13 * d0["mass"]
+        assert abs(d["energy"] - d0["energy"]) <= 1e-13 * abs(d0["energy"])
+
+
+def test_noble_abel_conserves_mass_energy_and_momentum():
+    """A disturbed Noble-Abel gas in a periodic box (no gravity): the totals of
+    mass, momentum and energy are unchanged to round-off (telescoping fluxes)."""
+    prob, U = I.random_periodic(2, (24, 20), seed=5, amp=0.2, mu=0.01, kappa=0.02)
+    prob = prob.replace(b=0.35, p_inf=0.4)
+    rho = U[0]
+    ke = 0.5 * (U[1] ** 2 + U[2] ** 2) / rho
+    p = (prob.gamma - 1.0) * (U[3] - ke)          # the pressure U was built with (ideal gas)
+    U = np.array(U)
+    U[3] = (p + prob.gamma * prob.p_inf) * (1.0 - prob.b * rho) / (prob.gamma - 1.0) + ke
+    d0 = O.diagnostics(prob, U)
+    V, _ = O.run(prob, U, 200)
+    d = O.diagnostics(prob, V)
+    for k in ("mass", "energy"):
+        assert abs(d[k] - d0[k]) <= 1e-13 * abs(d0[k]), k
+    for k in ("mom_x", "mom_y"):
+        assert abs(d[k] - d0[k]) <= 1e-13 * d0["mass"], k
+    assert d["max_speed"] > 1e-3     # it moved
+
+
+def test_noble_abel_zero_covolume_is_the_stiffened_gas_bitwise():
+    prob, U = I.stratified_random(2, (12, 10), seed=3, mu=0.01, kappa=0.02, p_inf=0.7)
+    assert prob.b == 0.0
+    a = O.step(prob, U, 1e-3)
+    b = O.step(prob.replace(b=-0.0), U, 1e-3)
+    assert np.array_equal(a, b)
+
+
+@pytest.mark.parametrize("axis", [0, 1])
+def test_noble_abel_uniform_flow_through_outflow_ends_stays_uniform(axis):
+    """A uniform Noble-Abel flow entering through one zero-gradient end and
+    leaving through the other: the inflow face carries the ghost's upwind
+    energy (rho e of the ghost from its p, with the covolume), so the state
+    stays uniform to round-off only if the ghost's energy follows the law."""
+    prob, U = I.sod(16, axis=axis, p_inf=0.3, b=0.4, left=(1.2, 0.8), right=(1.2, 0.8))
+    u = -0.35
+    U = np.array(U)
+    U[1 + axis] = U[0] * u
+    U[3] += 0.5 * U[0] * u * u
+    V, _ = O.run(prob, U, 50)
+    assert np.max(np.abs(V - U)) <= 1e-13 * np.max(np.abs(U))

@@ -1,7 +1,8 @@
 """The C oracle against an independent NumPy writing of the same 2D step
 (oracle/numpy_step.py) on grids of at most 16 x 16 cells: every boundary
 rule, gravity, dissipation, the low-Mach correction on and off, both energy
-variables (Sec. 2 and Appendix B) and the stiffened gas.  Two writings of one
+variables (Sec. 2 and Appendix B), the stiffened gas and the Noble-Abel
+stiffened gas.  Two writings of one
 specification, with different mechanisms (recursive per-cell ghosts and
 face arrays in C, padded whole-array expressions in NumPy), agree to
 rounding."""
@@ -29,7 +30,23 @@ CASES = {
     "rayleigh_taylor": lambda: I.rayleigh_taylor((8, 16)),
     "walls_n2": lambda: I.stratified_random(2, (5, 2), mu=0.01, kappa=0.01, chi=1.2),
     "stiffened_column": lambda: I.atmosphere((6, 16), p_inf=2.5),
+    "noble_abel_column": lambda: I.atmosphere((6, 16), p_inf=0.5, b=0.3),
+    "noble_abel_strat_noslip_visc": lambda: I.stratified_random(2, (16, 11), mu=0.01, kappa=0.02, p_inf=0.2, b=0.2),
+    "noble_abel_sod_x": lambda: I.sod(16, axis=0, p_inf=0.3, b=0.4),
+    "noble_abel_periodic_visc": lambda: (lambda pu: (pu[0].replace(b=0.3), pu[1]))(
+        I.random_periodic(2, (12, 10), seed=4, mu=0.02, kappa=0.03)),
+    "noble_abel_sod_y_inflow": lambda: _inflow(I.sod(16, axis=1, p_inf=0.3, b=0.4), -0.3),
 }
+
+
+def _inflow(pu, u):
+    """The tube with every cell moving at u along its axis (flow enters through one end)."""
+    prob, U = pu
+    axis = 0 if prob.n[0] > 1 else 1
+    U = np.array(U)
+    U[1 + axis] = U[0] * u
+    U[3] += 0.5 * U[0] * u * u
+    return prob, U
 
 
 def _cases():
