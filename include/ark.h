@@ -17,8 +17,9 @@
  * gravitational energy (Eq. 6, conservation_of_energy).  The equation of
  * state is the stiffened gas p = (gamma - 1) rho e - gamma p_inf,
  * T = (p + p_inf) / rho, c^2 = gamma (p + p_inf) / rho, which with p_inf = 0
- * is the ideal gas of Sec. 4 (Sec. 4 notes that the scheme takes another
- * equation of state).
+ * is the ideal gas of Sec. 4, or the Noble-Abel stiffened gas (a covolume b;
+ * see ark_eos); Sec. 4 notes that the scheme takes another equation of
+ * state.
  *
  * Conventions for every call:
  *   - Arrays are structure-of-arrays: field f of cell (i, j[, k]) is at
@@ -80,11 +81,36 @@ typedef struct {
     double lo[3], hi[3];       /* box corners                                         */
 } ark_grid;
 
+/* Equation of state (Sec. 4 uses the ideal gas and notes that the scheme
+ * admits another law).  With (gamma - 1) c_v = 1:
+ *   ARK_EOS_STIFFENED_GAS  p = (gamma-1) rho e - gamma p_inf,  T = (p + p_inf)/rho,
+ *                          c^2 = gamma (p + p_inf)/rho; p_inf = 0 is the ideal gas;
+ *   ARK_EOS_NOBLE_ABEL     the Noble-Abel stiffened gas, a covolume b leaving the
+ *                          fraction 1 - b rho of the volume free:
+ *                          p = (gamma-1) rho e / (1 - b rho) - gamma p_inf,
+ *                          T = (p + p_inf)(1 - b rho)/rho,
+ *                          c^2 = gamma (p + p_inf)/(rho (1 - b rho));
+ *                          b = 0 is the stiffened gas.
+ * The wall ghosts solve the discrete balance of Eq. 18 with the law's density
+ * rho(p, T).  The law is chosen per kernel instance, so the stiffened-gas
+ * path carries no covolume arithmetic. */
+enum {
+    ARK_EOS_STIFFENED_GAS = 0,
+    ARK_EOS_NOBLE_ABEL = 1
+};
+
 typedef struct {
     double gamma;              /* adiabatic index, > 1                                */
     double p_inf;              /* stiffened-gas constant, finite and >= 0 (0: ideal
                                   gas).  Physical states need rho > 0 and
                                   p + p_inf > 0; p itself may be negative.            */
+    int law;                   /* ARK_EOS_STIFFENED_GAS or ARK_EOS_NOBLE_ABEL          */
+    double b;                  /* covolume (ARK_EOS_NOBLE_ABEL), finite and >= 0;
+                                  physical states also need b rho < 1.  Must be 0
+                                  for ARK_EOS_STIFFENED_GAS.  With a covolume,
+                                  ARK_F64, ARK_F32 and ARK_F32_SPLIT take uniform
+                                  gravity only (no potential array); ensembles and
+                                  ark_compute_dt_noalloc take the stiffened gas. */
 } ark_eos;
 
 typedef struct {

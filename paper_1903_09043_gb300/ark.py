@@ -39,6 +39,9 @@ ARK_BC_OUTFLOW = 3
 ARK_F64 = 0
 ARK_F32 = 1
 ARK_F32_SPLIT = 2
+
+ARK_EOS_STIFFENED_GAS = 0
+ARK_EOS_NOBLE_ABEL = 1
 PRECISIONS = {"f64": ARK_F64, "f32": ARK_F32, "f32split": ARK_F32_SPLIT}
 
 
@@ -48,7 +51,8 @@ class ark_grid(ctypes.Structure):
 
 
 class ark_eos(ctypes.Structure):
-    _fields_ = [("gamma", ctypes.c_double), ("p_inf", ctypes.c_double)]
+    _fields_ = [("gamma", ctypes.c_double), ("p_inf", ctypes.c_double), ("law", ctypes.c_int),
+                ("b", ctypes.c_double)]
 
 
 class ark_gravity(ctypes.Structure):
@@ -154,6 +158,9 @@ def params_from_problem(prob, precision: int = ARK_F64) -> ark_params:
         p.bc.T_hi[d] = float(prob.T_hi[d])
     p.eos.gamma = float(prob.gamma)
     p.eos.p_inf = float(getattr(prob, "p_inf", 0.0))
+    b = float(getattr(prob, "b", 0.0))
+    p.eos.law = ARK_EOS_NOBLE_ABEL if b != 0.0 else ARK_EOS_STIFFENED_GAS
+    p.eos.b = b
     p.gravity.g = float(prob.g)
     phi = getattr(prob, "phi", None)
     if phi is not None:   # caller-supplied potential: a host array ark_create copies

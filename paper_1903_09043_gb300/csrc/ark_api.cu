@@ -52,6 +52,7 @@ ark::StepArgs ark::base_args(const ark_handle* h)
     }
     a.gamma = p.eos.gamma;
     a.p_inf = p.eos.p_inf;
+    a.b = p.eos.law == ARK_EOS_NOBLE_ABEL ? p.eos.b : 0.0;
     a.g = p.gravity.g;
     a.lo_v = p.grid.lo[h->dim - 1];
     a.mu = p.mu;
@@ -129,6 +130,16 @@ ark_status ark::validate_params(const ark_params* p, std::string& msg)
         msg = "eos.p_inf must be finite and >= 0";
         return ARK_ERR_INVALID_ARG;
     }
+    if (p->eos.law != ARK_EOS_STIFFENED_GAS && p->eos.law != ARK_EOS_NOBLE_ABEL) {
+        msg = "unknown eos.law"; return ARK_ERR_INVALID_ARG;
+    }
+    if (!(p->eos.b >= 0.0) || !std::isfinite(p->eos.b)) { msg = "eos.b must be finite and >= 0"; return ARK_ERR_INVALID_ARG; }
+    if (p->eos.law == ARK_EOS_STIFFENED_GAS && p->eos.b != 0.0) {
+        msg = "eos.b is the covolume of ARK_EOS_NOBLE_ABEL"; return ARK_ERR_INVALID_ARG;
+    }
+    if (p->eos.b != 0.0 && p->gravity.phi) {
+        msg = "a covolume takes uniform gravity only (no potential array)"; return ARK_ERR_UNSUPPORTED;
+    }
     if (!(p->K >= 1.0) || !std::isfinite(p->K)) { msg = "K must be finite and >= 1 (sub-characteristic condition)"; return ARK_ERR_INVALID_ARG; }
     if (!(p->cfl > 0.0) || !std::isfinite(p->cfl)) { msg = "cfl must be finite and > 0"; return ARK_ERR_INVALID_ARG; }
     if (!(p->mu >= 0.0) || !(p->kappa >= 0.0) || !std::isfinite(p->mu) || !std::isfinite(p->kappa)) {
@@ -171,8 +182,10 @@ bool ensure_stage(ark_handle* h, size_t bytes)
 void choose_launch(ark_handle* h, int nsm)
 {
     const int dim = h->dim;
-    h->kinfo = h->phiA ? ark::step_kernel_phi(dim, h->prec, h->visc)
-                       : (dim == 2 ? ark::step_kernel_2d(h->prec, h->visc) : ark::step_kernel_3d(h->prec, h->visc));
+    const bool covolume = h->p.eos.law == ARK_EOS_NOBLE_ABEL && h->p.eos.b != 0.0;
+    h->kinfo = h->phiA    ? ark::step_kernel_phi(dim, h->prec, h->visc)
+               : covolume ? ark::step_kernel_noble_abel(dim, h->prec, h->visc)
+               : (dim == 2 ? ark::step_kernel_2d(h->prec, h->visc) : ark::step_kernel_3d(h->prec, h->visc));
     h->tiles_x = (h->p.grid.n[0] + h->kinfo.tx - 1) / h->kinfo.tx;
     h->tiles_y = dim == 3 ? (h->p.grid.n[1] + h->kinfo.ty - 1) / h->kinfo.ty : 1;
     const int tiles = h->tiles_x * h->tiles_y;
@@ -356,8 +369,8 @@ ark_status ark_set_state(ark_handle* h, const double* U, int on_device)
         if (e != cudaSuccess) return cuda_fail(h, e, "base state");
         std::vector<double> rho(hm.begin(), hm.begin() + nv), pr(hm.begin() + nv, hm.end());
         for (int r = 0; r < nv; ++r)
-            if (!(rho[r] > 0.0) || !(pr[r] + h->p.eos.p_inf > 0.0))
-                return fail(h, ARK_ERR_NONPHYSICAL, "base state with rho <= 0 or p + p_inf <= 0");
+            if (!(rho[r] > 0.0) || !(pr[r] + h->p.eos.p_inf > 0.0) || !(a.b * rho[r] < 1.0))
+                return fail(h, ARK_ERR_NONPHYSICAL, "base state with rho <= 0, p + p_inf <= 0 or b rho >= 1");
         std::vector<double> b64;
         std::vector<float> tab;
         {
@@ -365,7 +378,7 @@ ark_status ark_set_state(ark_handle* h, const double* U, int on_device)
             const int V = h->dim - 1;
             ark::BaseSpec bs{nv, p.grid.lo[V], (p.grid.hi[V] - p.grid.lo[V]) / nv, p.gravity.g, p.eos.gamma, p.kappa,
                              p.bc.lo[V], p.bc.hi[V], p.bc.T_lo[V], p.bc.T_hi[V], p.eos.p_inf,
-                             h->phi_rows.empty() ? nullptr : h->phi_rows.data()};
+                             h->phi_rows.empty() ? nullptr : h->phi_rows.data(), a.b};
             ark::build_base_tables(bs, rho, pr, b64, tab);
         }
         e = cudaMemcpyAsync(h->base64, b64.data(), b64.size() * sizeof(double), cudaMemcpyHostToDevice, h->stream);

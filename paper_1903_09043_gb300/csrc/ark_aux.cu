@@ -19,7 +19,7 @@ __device__ __forceinline__ int row_of(const StepArgs& a, long long idx)
 // Wave rate of every cell; one atomicMax per block on the FP64 bit pattern
 // (positive doubles order like their bit patterns, so the result does not
 // depend on the order of the blocks).
-template <int D, typename Real, bool SPLIT, bool VISC>
+template <int D, typename Real, bool SPLIT, bool VISC, bool NA>
 __global__ void __launch_bounds__(AUX_THREADS) wave_rate_kernel(const __grid_constant__ StepArgs a, const Real* __restrict__ U,
                                                                   unsigned long long* slot)
 {
@@ -27,7 +27,7 @@ __global__ void __launch_bounds__(AUX_THREADS) wave_rate_kernel(const __grid_con
     const int nv = a.n[D - 1];
     const PhiRow<Real> ph(a);
     const KConst<Real> kc(a);
-    const Eos<Real> eos(kc);
+    const Eos<Real, NA> eos(kc);
     const Real mu = kc.mu, kappa = kc.kappa;
     const Real invdx[3] = {kc.invdx[0], kc.invdx[1], kc.invdx[2]};
     Real smax = Real(0);
@@ -108,7 +108,7 @@ __global__ void __launch_bounds__(AUX_THREADS) row_means_kernel(const StepArgs a
         }
         const double ke = 0.5 * m2 / rho;   // one FP64 division per cell
         accr += rho;
-        accp += (a.gamma - 1.0) * (U[(D + 1) * a.ncell + idx] - ke - rho * phi) - a.dgpinf;
+        accp += (a.gamma - 1.0) * (U[(D + 1) * a.ncell + idx] - ke - rho * phi) / (1.0 - a.b * rho) - a.dgpinf;
     }
     sr[threadIdx.x] = accr;
     sp[threadIdx.x] = accp;
@@ -158,7 +158,7 @@ __global__ void __launch_bounds__(AUX_THREADS) diag_kernel(const StepArgs a, con
             ke += 0.5 * rho * u * u;
             u2 += u * u;
         }
-        const double p = (a.gamma - 1.0) * (W - ke - rho * phi) - a.dgpinf;
+        const double p = (a.gamma - 1.0) * (W - ke - rho * phi) / (1.0 - a.b * rho) - a.dgpinf;   // covolume b
         acc[DG_MASS] += rho;
         acc[DG_MX] += m[0];
         acc[DG_MY] += m[1];
@@ -222,7 +222,12 @@ cudaError_t launch_wave_rate(const StepArgs& a, int prec, int visc, const void* 
                              cudaStream_t s)
 {
     const int g = grid_for(a.ncell);
-#define ARK_WR(D, R, SP, VI) wave_rate_kernel<D, R, SP, VI><<<g, AUX_THREADS, 0, s>>>(a, (const R*)U, slot)
+    // a covolume takes the Noble-Abel instances; b = 0 is the stiffened gas
+#define ARK_WR(D, R, SP, VI)                                                                    \
+    do {                                                                                        \
+        if (a.b != 0.0) wave_rate_kernel<D, R, SP, VI, true><<<g, AUX_THREADS, 0, s>>>(a, (const R*)U, slot); \
+        else wave_rate_kernel<D, R, SP, VI, false><<<g, AUX_THREADS, 0, s>>>(a, (const R*)U, slot);           \
+    } while (0)
     if (a.dim == 2) {
         if (prec == P_F64) { if (visc) ARK_WR(2, double, false, true); else ARK_WR(2, double, false, false); }
         else if (prec == P_F32) { if (visc) ARK_WR(2, float, false, true); else ARK_WR(2, float, false, false); }

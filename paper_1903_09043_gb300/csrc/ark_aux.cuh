@@ -38,6 +38,7 @@ struct StepKernelInfo {
 StepKernelInfo step_kernel_2d(int prec, int visc);
 StepKernelInfo step_kernel_3d(int prec, int visc);
 StepKernelInfo step_kernel_phi(int dim, int prec, int visc);   // caller-supplied potential array
+StepKernelInfo step_kernel_noble_abel(int dim, int prec, int visc);   // covolume (Noble-Abel stiffened gas)
 
 // Batched 2D step-kernel instances (ark_batch_2d*.cu): tile widths 64, 128, 256.
 struct BatchKernelInfo {

@@ -1,6 +1,7 @@
 // ark_base.h -- FP64 base state of the F32_SPLIT form (host code).
 #pragma once
 
+#include <cmath>
 #include <vector>
 
 #include "ark_common.cuh"
@@ -16,6 +17,7 @@ struct BaseSpec {
     double p_inf;        // stiffened-gas constant (0: ideal gas)
     const double* phi_rows = nullptr;   // potential of rows -2 .. nv + 1 (nv + 4 values), or
                                         // nullptr for uniform gravity, Phi = -g x_last
+    double b = 0.0;      // covolume of the Noble-Abel stiffened gas (0: the stiffened gas)
 };
 
 // FP64 base state of F32_SPLIT: rows -2 .. nv + 1 from the interior row means,
@@ -35,7 +37,7 @@ inline void build_base_tables(const BaseSpec& s, const std::vector<double>& rho_
     for (int r = 0; r < nv; ++r) {
         rho[r + 2] = rho_in[r];
         pr[r + 2] = p_in[r];
-        T[r + 2] = (p_in[r] + s.p_inf) / rho_in[r];
+        T[r + 2] = (p_in[r] + s.p_inf) * (1.0 - s.b * rho_in[r]) / rho_in[r];
     }
     for (int side = 0; side < 2; ++side) {
         const int bc = side == 0 ? s.bc_lo : s.bc_hi;
@@ -53,9 +55,16 @@ inline void build_base_tables(const BaseSpec& s, const std::vector<double>& rho_
             } else {
                 const double Tg = bc == BC_REFLECT ? T[m + 2] : 2.0 * Tw - T[m + 2];
                 const double dphi = phi[g + 2] - phi[A + 2];
-                const double pe = (pr[A + 2] + s.p_inf - 0.5 * rho[A + 2] * dphi) / (1.0 + dphi / (2.0 * Tg));
+                const double K = pr[A + 2] + s.p_inf - 0.5 * rho[A + 2] * dphi;
+                double pe;
+                if (s.b == 0.0) {
+                    pe = K / (1.0 + dphi / (2.0 * Tg));
+                } else {   // rho = pe / (T + b pe): the balance is a quadratic in pe (positive root)
+                    const double B = Tg - s.b * K + 0.5 * dphi;
+                    pe = 2.0 * K * Tg / (B + std::sqrt(B * B + 4.0 * s.b * K * Tg));
+                }
                 pr[g + 2] = pe - s.p_inf;
-                rho[g + 2] = pe / Tg;
+                rho[g + 2] = pe / (Tg + s.b * pe);
                 T[g + 2] = Tg;
             }
         }
@@ -63,7 +72,7 @@ inline void build_base_tables(const BaseSpec& s, const std::vector<double>& rho_
     b64.assign(4 * L, 0.0);
     std::vector<double> W0(L);
     for (int i = 0; i < L; ++i) {
-        W0[i] = (pr[i] + s.gamma * s.p_inf) / gm1 + rho[i] * phi[i];
+        W0[i] = (pr[i] + s.gamma * s.p_inf) * (1.0 - s.b * rho[i]) / gm1 + rho[i] * phi[i];
         b64[0 * L + i] = rho[i];
         b64[1 * L + i] = pr[i];
         b64[2 * L + i] = W0[i];

@@ -42,6 +42,7 @@ struct StepArgs {
     double dx[3];           // cell sizes
     double gamma;
     double p_inf;           // stiffened-gas constant (0: ideal gas)
+    double b;               // covolume of the Noble-Abel stiffened gas (0: the stiffened gas)
     double g;               // gravity along the last axis: Phi = -g x_last
     double lo_v;            // lower coordinate of the last axis
     double mu, kappa, K, cfl;
@@ -67,7 +68,7 @@ struct StepArgs {
     // constants of the stencil in both precisions, rounded once on the host, so
     // that no kernel converts between precisions (conversions run on GB300's
     // FP64 pipe, 1/64 of its FP32 rate)
-    float fK, fhalfInvK, fmu, fkappa, feta, fgamma, fgm1, fpinf, fgpinf, fphi_g, fphi_lo, fphi_dv, finvdx[3];
+    float fK, fhalfInvK, fmu, fkappa, feta, fgamma, fgm1, fpinf, fgpinf, fb, fphi_g, fphi_lo, fphi_dv, finvdx[3];
     float fdphi;            // Phi_{r+1} - Phi_r = -g dz, formed in FP64 (uniform g)
     double dK, dhalfInvK, deta, dgpinf, dinvdx[3];
 };
@@ -90,6 +91,7 @@ inline void fill_constants(StepArgs& a)
     a.fgm1 = (float)(a.gamma - 1.0);
     a.fpinf = (float)a.p_inf;
     a.fgpinf = (float)a.dgpinf;
+    a.fb = (float)a.b;
     a.fphi_g = (float)a.g;
     a.fphi_lo = (float)a.lo_v;
     a.fphi_dv = (float)a.dx[V];

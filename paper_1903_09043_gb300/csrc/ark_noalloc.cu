@@ -122,6 +122,7 @@ extern "C" ark_status ark_compute_dt_noalloc(const ark_params* p, const double* 
     if (vs != ARK_OK) return vs;
     if (p->precision != ARK_F64) return ARK_ERR_INVALID_ARG;
     if (p->gravity.phi) return ARK_ERR_UNSUPPORTED;   // the potential array would need a device copy
+    if (p->eos.law != ARK_EOS_STIFFENED_GAS) return ARK_ERR_UNSUPPORTED;   // the stiffened-gas rate only
     const int dim = p->grid.dim;
     long long ncell = 1;
     ark::StepArgs a;

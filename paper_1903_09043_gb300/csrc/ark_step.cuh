@@ -185,17 +185,17 @@ template <typename Real>
 struct KConst;
 template <>
 struct KConst<float> {
-    float K, halfInvK, mu, kappa, eta, gamma, gm1, pinf, gpinf, invdx[3];
+    float K, halfInvK, mu, kappa, eta, gamma, gm1, pinf, gpinf, b, invdx[3];
     __device__ explicit KConst(const StepArgs& a)
         : K(a.fK), halfInvK(a.fhalfInvK), mu(a.fmu), kappa(a.fkappa), eta(a.feta), gamma(a.fgamma), gm1(a.fgm1),
-          pinf(a.fpinf), gpinf(a.fgpinf), invdx{a.finvdx[0], a.finvdx[1], a.finvdx[2]} {}
+          pinf(a.fpinf), gpinf(a.fgpinf), b(a.fb), invdx{a.finvdx[0], a.finvdx[1], a.finvdx[2]} {}
 };
 template <>
 struct KConst<double> {
-    double K, halfInvK, mu, kappa, eta, gamma, gm1, pinf, gpinf, invdx[3];
+    double K, halfInvK, mu, kappa, eta, gamma, gm1, pinf, gpinf, b, invdx[3];
     __device__ explicit KConst(const StepArgs& a)
         : K(a.dK), halfInvK(a.dhalfInvK), mu(a.mu), kappa(a.kappa), eta(a.deta), gamma(a.gamma), gm1(a.gamma - 1.0),
-          pinf(a.p_inf), gpinf(a.dgpinf), invdx{a.dinvdx[0], a.dinvdx[1], a.dinvdx[2]} {}
+          pinf(a.p_inf), gpinf(a.dgpinf), b(a.b), invdx{a.dinvdx[0], a.dinvdx[1], a.dinvdx[2]} {}
 };
 
 // Equation of state: the stiffened gas (Harlow and Amsden 1971; temperature
@@ -207,10 +207,26 @@ struct KConst<double> {
 // Every formula below reads the pressure either as a difference or as the
 // effective pressure pe = p + p_inf.  In F32_SPLIT the base row carries
 // pe0 = p0 + p_inf (B_P0), so deviations need no p_inf term at all.
-template <typename Real>
+// NA: the Noble-Abel stiffened gas (Le Metayer and Saurel 2016, without the
+// reference energy), a second law of the same family: the covolume b leaves
+// the fraction fv = 1 - b rho of the volume free,
+//   p = (gamma-1) rho e / fv - gamma p_inf,  T = (p + p_inf) fv / rho,
+//   c^2 = gamma (p + p_inf) / (rho fv);
+// b = 0 is the stiffened gas.  The law is chosen per kernel instance (a
+// template flag), so the stiffened-gas instances carry no covolume term.
+template <typename Real, bool NA_ = false>
 struct Eos {
+    static constexpr bool NA = false;
     Real gamma, gm1, pinf, gpinf;   // gpinf = gamma p_inf
     __device__ explicit Eos(const KConst<Real>& k) : gamma(k.gamma), gm1(k.gm1), pinf(k.pinf), gpinf(k.gpinf) {}
+};
+template <typename Real>
+struct Eos<Real, true> {
+    static constexpr bool NA = true;
+    Real gamma, gm1, pinf, gpinf;   // gpinf = gamma p_inf
+    Real b;                         // covolume
+    __device__ explicit Eos(const KConst<Real>& k)
+        : gamma(k.gamma), gm1(k.gm1), pinf(k.pinf), gpinf(k.gpinf), b(k.b) {}
 };
 
 // Phi at the centre of row r of the gravity axis (Phi = -g x_last), in the
@@ -246,8 +262,12 @@ __device__ __forceinline__ Row<Real> row_info(const StepArgs& a, const PhiRow<Re
 }
 
 // Primitive values from conserved values (the equation of state above).
-template <int D, typename Real, bool SPLIT>
-__device__ __forceinline__ void prim(Cell<D, Real>& c, const Row<Real>& w, const Eos<Real>& q)
+// Split form with a covolume: with re = rho e - rho0 e0 (the stored deviation),
+//   dp = ((gamma-1) re + b (p0 + gamma p_inf) drho) / fv,
+//   dT = (dp fv - (T0 + b pe0) drho) / rho,
+// exact rearrangements of the law about the base row, O(deviation) throughout.
+template <int D, typename Real, bool SPLIT, bool NA>
+__device__ __forceinline__ void prim(Cell<D, Real>& c, const Row<Real>& w, const Eos<Real, NA>& q)
 {
     c.rho = SPLIT ? w.rho0 + c.drho : c.drho;
     const Real rr = rcp(c.rho);
@@ -259,15 +279,24 @@ __device__ __forceinline__ void prim(Cell<D, Real>& c, const Row<Real>& w, const
         ke += c.m[d] * c.u[d];
     }
     const Real re = c.dW - Real(0.5) * ke - c.drho * w.phi;
-    c.dp = SPLIT ? q.gm1 * re : q.gm1 * re - q.gpinf;
-    const Real pe = SPLIT ? w.p0 + c.dp : c.dp + q.pinf;
-    c.dT = SPLIT ? (c.dp - w.T0 * c.drho) * rr : pe * rr;
-    sqrt_rsqrt(q.gamma * pe * rr, c.c, c.rc);
+    if constexpr (NA) {
+        const Real fv = Real(1) - q.b * c.rho;
+        const Real rfv = rcp(fv);
+        c.dp = SPLIT ? (q.gm1 * re + q.b * (w.p0 + q.gm1 * q.pinf) * c.drho) * rfv : q.gm1 * re * rfv - q.gpinf;
+        const Real pe = SPLIT ? w.p0 + c.dp : c.dp + q.pinf;
+        c.dT = SPLIT ? (c.dp * fv - (w.T0 + q.b * w.p0) * c.drho) * rr : pe * fv * rr;
+        sqrt_rsqrt(q.gamma * pe * rr * rfv, c.c, c.rc);
+    } else {
+        c.dp = SPLIT ? q.gm1 * re : q.gm1 * re - q.gpinf;
+        const Real pe = SPLIT ? w.p0 + c.dp : c.dp + q.pinf;
+        c.dT = SPLIT ? (c.dp - w.T0 * c.drho) * rr : pe * rr;
+        sqrt_rsqrt(q.gamma * pe * rr, c.c, c.rc);
+    }
 }
 
 // Conserved values of a ghost built from primitives (rho full, u, dp, dT).
-template <int D, typename Real, bool SPLIT>
-__device__ __forceinline__ void cons_from_prim(Cell<D, Real>& g, const Row<Real>& w, const Eos<Real>& q)
+template <int D, typename Real, bool SPLIT, bool NA>
+__device__ __forceinline__ void cons_from_prim(Cell<D, Real>& g, const Row<Real>& w, const Eos<Real, NA>& q)
 {
     Real ke = Real(0);
 #pragma unroll
@@ -275,11 +304,23 @@ __device__ __forceinline__ void cons_from_prim(Cell<D, Real>& g, const Row<Real>
         g.m[d] = g.rho * g.u[d];
         ke += g.rho * g.u[d] * g.u[d];
     }
-    // rho e = (p + gamma p_inf) / (gamma - 1); the deviation form cancels gamma p_inf
-    g.dW = (SPLIT ? g.dp : g.dp + q.gpinf) / q.gm1 + Real(0.5) * ke + g.drho * w.phi;
-    const Real pe = SPLIT ? w.p0 + g.dp : g.dp + q.pinf;
-    g.rr = rcp(g.rho);
-    sqrt_rsqrt(q.gamma * pe * g.rr, g.c, g.rc);
+    if constexpr (NA) {
+        // rho e = (p + gamma p_inf) fv / (gamma - 1); about the base row,
+        // re = (dp fv - b (p0 + gamma p_inf) drho) / (gamma - 1)
+        const Real fv = Real(1) - q.b * g.rho;
+        const Real re = SPLIT ? (g.dp * fv - q.b * (w.p0 + q.gm1 * q.pinf) * g.drho) / q.gm1
+                              : (g.dp + q.gpinf) * fv / q.gm1;
+        g.dW = re + Real(0.5) * ke + g.drho * w.phi;
+        const Real pe = SPLIT ? w.p0 + g.dp : g.dp + q.pinf;
+        g.rr = rcp(g.rho);
+        sqrt_rsqrt(q.gamma * pe * g.rr * rcp(fv), g.c, g.rc);
+    } else {
+        // rho e = (p + gamma p_inf) / (gamma - 1); the deviation form cancels gamma p_inf
+        g.dW = (SPLIT ? g.dp : g.dp + q.gpinf) / q.gm1 + Real(0.5) * ke + g.drho * w.phi;
+        const Real pe = SPLIT ? w.p0 + g.dp : g.dp + q.pinf;
+        g.rr = rcp(g.rho);
+        sqrt_rsqrt(q.gamma * pe * g.rr, g.c, g.rc);
+    }
 }
 
 // Wall ghost (reflective hydrostatic or no-slip fixed-temperature): velocity
@@ -291,10 +332,22 @@ __device__ __forceinline__ void cons_from_prim(Cell<D, Real>& g, const Row<Real>
 // in deviation form, with base ghost row (rho0_g, T0_g) built by the same rule,
 //   dp_g = (dp_A - dPhi drho_A / 2 + dPhi rho0_g dT_g / (2 T_g)) / (1 + dPhi / (2 T_g)),
 //   drho_g = (dp_g - rho0_g dT_g) / T_g.
-template <int D, typename Real, bool SPLIT>
+//
+// NA (covolume b): rho_g = pe_g / (T_g + b pe_g), so the balance is the
+// quadratic b pe^2 + (T_g - b K + dPhi/2) pe - K T_g = 0, K = pe_A - rho_A dPhi / 2,
+// solved by its positive root 2 K T_g / (B + sqrt(B^2 + 4 b K T_g)), B the
+// linear coefficient (no cancellation).  In deviation form, with the base ghost
+// row q0 = pe0_g, T0_g (the base quadratic with K0 = q0 + rho0_g dPhi / 2) and
+// dK = dp_A - drho_A dPhi / 2, the deviation dp_g solves
+//   b dp^2 + beta dp + g1 = 0,  beta = 2 b q0 + T0_g - b K0 + dPhi/2 + dT_g - b dK,
+//   g1 = (dT_g - b dK) q0 - K0 dT_g - dK (T0_g + dT_g),
+// dp_g = -2 g1 / (beta + sqrt(beta^2 - 4 b g1)), and
+//   drho_g = (dp_g T0_g - q0 dT_g) / ((T_g + b pe_g) (T0_g + b q0));
+// both reduce term by term to the lines above when b = 0.
+template <int D, typename Real, bool SPLIT, bool NA>
 __device__ __forceinline__ Cell<D, Real> wall_ghost(const Cell<D, Real>& M, const Cell<D, Real>& A, int bc,
                                                     int axis, Real Tw, const Row<Real>& wg, Real dphi,
-                                                    const Eos<Real>& q)
+                                                    const Eos<Real, NA>& q)
 {
     Cell<D, Real> g;
 #pragma unroll
@@ -303,11 +356,30 @@ __device__ __forceinline__ Cell<D, Real> wall_ghost(const Cell<D, Real>& M, cons
     if (bc == BC_REFLECT) dTg = M.dT;
     else dTg = SPLIT ? -M.dT : Real(2) * Tw - M.dT;
     const Real Tg = SPLIT ? wg.T0 + dTg : dTg;
-    Real num = (SPLIT ? A.dp : A.dp + q.pinf) - Real(0.5) * A.drho * dphi;
-    if constexpr (SPLIT) num += Real(0.5) * wg.rho0 * dphi * dTg / Tg;
-    const Real x = num / (Real(1) + dphi / (Real(2) * Tg));   // dp_g (split) or pe_g
-    g.dp = SPLIT ? x : x - q.pinf;
-    g.drho = SPLIT ? (x - wg.rho0 * dTg) / Tg : x / Tg;
+    if constexpr (NA) {
+        if constexpr (SPLIT) {
+            const Real q0 = wg.p0, T0 = wg.T0;
+            const Real K0 = q0 + Real(0.5) * wg.rho0 * dphi;
+            const Real dK = A.dp - Real(0.5) * A.drho * dphi;
+            const Real beta = Real(2) * q.b * q0 + T0 - q.b * K0 + Real(0.5) * dphi + dTg - q.b * dK;
+            const Real g1 = (dTg - q.b * dK) * q0 - K0 * dTg - dK * (T0 + dTg);
+            const Real x = Real(-2) * g1 / (beta + vsqrt(beta * beta - Real(4) * q.b * g1));
+            g.dp = x;
+            g.drho = (x * T0 - q0 * dTg) / ((Tg + q.b * (q0 + x)) * (T0 + q.b * q0));
+        } else {
+            const Real K = A.dp + q.pinf - Real(0.5) * A.drho * dphi;
+            const Real B = Tg - q.b * K + Real(0.5) * dphi;
+            const Real pe = Real(2) * K * Tg / (B + vsqrt(B * B + Real(4) * q.b * K * Tg));
+            g.dp = pe - q.pinf;
+            g.drho = pe / (Tg + q.b * pe);
+        }
+    } else {
+        Real num = (SPLIT ? A.dp : A.dp + q.pinf) - Real(0.5) * A.drho * dphi;
+        if constexpr (SPLIT) num += Real(0.5) * wg.rho0 * dphi * dTg / Tg;
+        const Real x = num / (Real(1) + dphi / (Real(2) * Tg));   // dp_g (split) or pe_g
+        g.dp = SPLIT ? x : x - q.pinf;
+        g.drho = SPLIT ? (x - wg.rho0 * dTg) / Tg : x / Tg;
+    }
     g.dT = dTg;
     g.rho = SPLIT ? wg.rho0 + g.drho : g.drho;
     cons_from_prim<D, Real, SPLIT>(g, wg, q);
@@ -319,8 +391,8 @@ __device__ __forceinline__ Cell<D, Real> wall_ghost(const Cell<D, Real>& M, cons
 // b holds the cell's stored values (deviation form in F32_SPLIT); the
 // effective pressure pe = p + p_inf and rho are returned for the physical
 // checks (both must be positive).
-template <int D, typename Real, bool SPLIT, bool VISC>
-__device__ __forceinline__ Real wave_rate(const Real* b, const Row<Real>& w, const Eos<Real>& q,
+template <int D, typename Real, bool SPLIT, bool VISC, bool NA>
+__device__ __forceinline__ Real wave_rate(const Real* b, const Row<Real>& w, const Eos<Real, NA>& q,
                                           const Real* invdx, Real mu, Real kappa, Real& pe, Real& rho)
 {
     rho = SPLIT ? w.rho0 + b[0] : b[0];
@@ -333,10 +405,17 @@ __device__ __forceinline__ Real wave_rate(const Real* b, const Row<Real>& w, con
         ke += b[1 + d] * uu[d];
     }
     const Real re = b[D + 1] - Real(0.5) * ke - b[0] * w.phi;
-    const Real dp = SPLIT ? q.gm1 * re : q.gm1 * re - q.gpinf;
-    pe = SPLIT ? w.p0 + dp : dp + q.pinf;
     Real cs, rcs;
-    sqrt_rsqrt(q.gamma * pe * rr, cs, rcs);
+    if constexpr (NA) {   // covolume: the law of prim()
+        const Real rfv = rcp(Real(1) - q.b * rho);
+        const Real dp = SPLIT ? (q.gm1 * re + q.b * (w.p0 + q.gm1 * q.pinf) * b[0]) * rfv : q.gm1 * re * rfv - q.gpinf;
+        pe = SPLIT ? w.p0 + dp : dp + q.pinf;
+        sqrt_rsqrt(q.gamma * pe * rr * rfv, cs, rcs);
+    } else {
+        const Real dp = SPLIT ? q.gm1 * re : q.gm1 * re - q.gpinf;
+        pe = SPLIT ? w.p0 + dp : dp + q.pinf;
+        sqrt_rsqrt(q.gamma * pe * rr, cs, rcs);
+    }
 #pragma unroll
     for (int d = 0; d < D; ++d) sh += (vabs(uu[d]) + cs) * invdx[d];
     if constexpr (VISC) {
@@ -383,7 +462,7 @@ __device__ Real phi_resolve(const StepArgs& a, const Real* __restrict__ P, int i
 // Loader of any cell within two layers of the tile, boundary rules included.
 // PHIA: the potential is the caller's array (phi_resolve) instead of -g x_last,
 // so ghosts across in-plane walls see its jumps too.
-template <int DIM, typename Real, bool SPLIT, bool VISC, int TX, int TY, bool PHIA = false>
+template <int DIM, typename Real, bool SPLIT, bool VISC, int TX, int TY, bool PHIA = false, bool NA = false>
 struct Stepper {
     using C = StepCfg<DIM, Real, SPLIT, VISC, TX, TY>;
     static constexpr int D = DIM;
@@ -395,7 +474,7 @@ struct Stepper {
     long long N;
     int nx, ny, nv;
     PhiRow<Real> phi;
-    Eos<Real> eos;
+    Eos<Real, NA> eos;
 
     __device__ Stepper(const StepArgs& args) : a(args), phi(args), eos(KConst<Real>(args))
     {
@@ -596,8 +675,8 @@ __device__ __forceinline__ void store_cell(const Cell<D, Real>& x, Real* vT, Rea
 // Cells of ghost planes and of tiles that touch the box edge: boundary rules,
 // out of line so that the interior path stays in registers.
 // PHIA: the cell's density and potential also go to the ring ph (rho, Phi).
-template <int DIM, typename Real, bool SPLIT, bool VISC, int TX, int TY, bool PHIA = false>
-__device__ __noinline__ void slow_cell(const Stepper<DIM, Real, SPLIT, VISC, TX, TY, PHIA> S, int gx, int gy, int f,
+template <int DIM, typename Real, bool SPLIT, bool VISC, int TX, int TY, bool PHIA = false, bool NA = false>
+__device__ __noinline__ void slow_cell(const Stepper<DIM, Real, SPLIT, VISC, TX, TY, PHIA, NA> S, int gx, int gy, int f,
                                        Real* vT, Real* ff, Real* uc, Real* ph, int c, int lx, int ly)
 {
     using C = StepCfg<DIM, Real, SPLIT, VISC, TX, TY, PHIA>;
@@ -613,7 +692,7 @@ __device__ __noinline__ void slow_cell(const Stepper<DIM, Real, SPLIT, VISC, TX,
 // gravity axis; `lead` marks the one share per step that advances the clock.
 // Called by the single-grid kernel (runs of planes of a balanced schedule) and
 // by the batched kernel (work items of many runs).
-template <int DIM, typename Real, bool SPLIT, bool VISC, int TX, int TY, bool PHIA = false>
+template <int DIM, typename Real, bool SPLIT, bool VISC, int TX, int TY, bool PHIA = false, bool NA = false>
 __device__ __forceinline__ void step_block(const StepArgs& a, const int tile, const int z0, const int z1,
                                            const bool lead, unsigned char* smem_raw)
 {
@@ -624,7 +703,7 @@ __device__ __forceinline__ void step_block(const StepArgs& a, const int tile, co
     Real* sm = reinterpret_cast<Real*>(smem_raw);
     double* red = reinterpret_cast<double*>(smem_raw + ((C::N_REAL * sizeof(Real) + 15) / 16) * 16);
 
-    const Stepper<DIM, Real, SPLIT, VISC, TX, TY, PHIA> S(a);
+    const Stepper<DIM, Real, SPLIT, VISC, TX, TY, PHIA, NA> S(a);
     const int tid = threadIdx.x;
     const int x0 = (tile % a.tiles_x) * TX;
     const int y0 = D == 3 ? (tile / a.tiles_x) * TY : 0;
@@ -758,7 +837,7 @@ __device__ __forceinline__ void step_block(const StepArgs& a, const int tile, co
                         ph_f[NR2 + c] = rawphi[s];
                     }
                 } else {
-                    slow_cell<DIM, Real, SPLIT, VISC, TX, TY, PHIA>(S, sgx[s], sgy[s], f, vT_f, ff_f, uc_f, ph_f, c, lx, ly);
+                    slow_cell<DIM, Real, SPLIT, VISC, TX, TY, PHIA, NA>(S, sgx[s], sgy[s], f, vT_f, ff_f, uc_f, ph_f, c, lx, ly);
                 }
             }
         }
@@ -1092,7 +1171,7 @@ __device__ __forceinline__ void step_block(const StepArgs& a, const int tile, co
 // of resident blocks, and block b marches units [b W, (b + 1) W) of the
 // tile-major list of (tile, plane) units, as one run of planes per tile it
 // touches (W = work_per_block).
-template <int DIM, typename Real, bool SPLIT, bool VISC, int TX, int TY, bool PHIA = false>
+template <int DIM, typename Real, bool SPLIT, bool VISC, int TX, int TY, bool PHIA = false, bool NA = false>
 __global__ void __launch_bounds__(TX * TY, sizeof(Real) == 8 ? 1 : 2)
 ark_step_kernel(const __grid_constant__ StepArgs a)
 {
@@ -1106,7 +1185,7 @@ ark_step_kernel(const __grid_constant__ StepArgs a)
         const int tile = (int)(u / nv);
         const int z0 = (int)(u - (long long)tile * nv);
         const int z1 = (int)min((long long)nv, z0 + (end - u));
-        step_block<DIM, Real, SPLIT, VISC, TX, TY, PHIA>(a, tile, z0, z1, lead, smem_raw);
+        step_block<DIM, Real, SPLIT, VISC, TX, TY, PHIA, NA>(a, tile, z0, z1, lead, smem_raw);
         u += z1 - z0;
         lead = false;
         __syncthreads();   // the next run reuses the shared plane rings

@@ -117,7 +117,7 @@ __device__ __forceinline__ void flux_update_n(float* c, const float* a, float s,
     }
 }
 
-template <int DIM, typename Real, bool SPLIT, bool VISC, int R2X, int R2Y, bool PHIA = false>
+template <int DIM, typename Real, bool SPLIT, bool VISC, int R2X, int R2Y, bool PHIA = false, bool NA = false>
 __device__ __forceinline__ void step_block2(const StepArgs& a, const int tile, const int z0, const int z1, const bool lead,
                                             unsigned char* smem_raw)
 {
@@ -128,7 +128,7 @@ __device__ __forceinline__ void step_block2(const StepArgs& a, const int tile, c
     double* red = reinterpret_cast<double*>(smem_raw + C::O_RED);
     float* const bring = reinterpret_cast<float*>(smem_raw + C::O_BASE);
 
-    const Stepper<DIM, Real, SPLIT, VISC, C::TX, C::TY, PHIA> S(a);
+    const Stepper<DIM, Real, SPLIT, VISC, C::TX, C::TY, PHIA, NA> S(a);
     constexpr int NFF = C::NFF;
     const int t = threadIdx.x;
     const int lx = t % R2X - 2, ly = t / R2X - C::HY;
@@ -738,7 +738,7 @@ __device__ __forceinline__ void step_block2(const StepArgs& a, const int tile, c
     if (status) atomicOr(a.status, status);
 }
 
-template <int DIM, typename Real, bool SPLIT, bool VISC, int R2X, int R2Y, bool PHIA = false>
+template <int DIM, typename Real, bool SPLIT, bool VISC, int R2X, int R2Y, bool PHIA = false, bool NA = false>
 __global__ void __launch_bounds__(R2X * R2Y, 512 / (R2X * R2Y)) ark_step2_kernel(const __grid_constant__ StepArgs a)
 {
     extern __shared__ __align__(16) unsigned char smem_raw[];
@@ -753,7 +753,7 @@ __global__ void __launch_bounds__(R2X * R2Y, 512 / (R2X * R2Y)) ark_step2_kernel
         const int tile = (int)(u / nv);
         const int z0 = (int)(u - (long long)tile * nv);
         const int z1 = (int)min((long long)nv, z0 + (end - u));
-        step_block2<DIM, Real, SPLIT, VISC, R2X, R2Y, PHIA>(a, tile, z0, z1, lead, smem_raw);
+        step_block2<DIM, Real, SPLIT, VISC, R2X, R2Y, PHIA, NA>(a, tile, z0, z1, lead, smem_raw);
         u += z1 - z0;
         lead = false;
         __syncthreads();   // the next run reuses the shared exchange arrays

@@ -6,7 +6,7 @@
 
 namespace ark {
 
-template <int DIM, typename Real, bool SPLIT, bool VISC, int R2X, int R2Y, bool PHIA = false>
+template <int DIM, typename Real, bool SPLIT, bool VISC, int R2X, int R2Y, bool PHIA = false, bool NA = false>
 cudaError_t launch_step2_impl(const StepArgs& a, dim3 grid, cudaStream_t s)
 {
     using C = Step2Cfg<DIM, Real, SPLIT, VISC, R2X, R2Y, PHIA>;
@@ -15,21 +15,21 @@ cudaError_t launch_step2_impl(const StepArgs& a, dim3 grid, cudaStream_t s)
     cudaError_t e = cudaGetDevice(&dev);
     if (e != cudaSuccess) return e;
     if (attr_device != dev) {
-        e = cudaFuncSetAttribute(ark_step2_kernel<DIM, Real, SPLIT, VISC, R2X, R2Y, PHIA>,
+        e = cudaFuncSetAttribute(ark_step2_kernel<DIM, Real, SPLIT, VISC, R2X, R2Y, PHIA, NA>,
                                  cudaFuncAttributeMaxDynamicSharedMemorySize, (int)C::SMEM_BYTES);
         if (e != cudaSuccess) return e;
         attr_device = dev;
     }
-    ark_step2_kernel<DIM, Real, SPLIT, VISC, R2X, R2Y, PHIA><<<grid, C::NT, C::SMEM_BYTES, s>>>(a);
+    ark_step2_kernel<DIM, Real, SPLIT, VISC, R2X, R2Y, PHIA, NA><<<grid, C::NT, C::SMEM_BYTES, s>>>(a);
     return cudaGetLastError();
 }
 
-template <int DIM, typename Real, bool SPLIT, bool VISC, int R2X, int R2Y, bool PHIA = false>
+template <int DIM, typename Real, bool SPLIT, bool VISC, int R2X, int R2Y, bool PHIA = false, bool NA = false>
 StepKernelInfo step2_info()
 {
     using C = Step2Cfg<DIM, Real, SPLIT, VISC, R2X, R2Y, PHIA>;
     StepKernelInfo k;
-    k.launch = &launch_step2_impl<DIM, Real, SPLIT, VISC, R2X, R2Y, PHIA>;
+    k.launch = &launch_step2_impl<DIM, Real, SPLIT, VISC, R2X, R2Y, PHIA, NA>;
     k.tx = C::TX;
     k.ty = C::TY;
     k.threads = C::NT;

@@ -6,7 +6,7 @@
 
 namespace ark {
 
-template <int DIM, typename Real, bool SPLIT, bool VISC, int TX, int TY, bool PHIA = false>
+template <int DIM, typename Real, bool SPLIT, bool VISC, int TX, int TY, bool PHIA = false, bool NA = false>
 cudaError_t launch_step_impl(const StepArgs& a, dim3 grid, cudaStream_t s)
 {
     using C = StepCfg<DIM, Real, SPLIT, VISC, TX, TY, PHIA>;
@@ -15,21 +15,21 @@ cudaError_t launch_step_impl(const StepArgs& a, dim3 grid, cudaStream_t s)
     cudaError_t e = cudaGetDevice(&dev);
     if (e != cudaSuccess) return e;
     if (attr_device != dev) {
-        e = cudaFuncSetAttribute(ark_step_kernel<DIM, Real, SPLIT, VISC, TX, TY, PHIA>,
+        e = cudaFuncSetAttribute(ark_step_kernel<DIM, Real, SPLIT, VISC, TX, TY, PHIA, NA>,
                                  cudaFuncAttributeMaxDynamicSharedMemorySize, (int)C::SMEM_BYTES);
         if (e != cudaSuccess) return e;
         attr_device = dev;
     }
-    ark_step_kernel<DIM, Real, SPLIT, VISC, TX, TY, PHIA><<<grid, C::NT, C::SMEM_BYTES, s>>>(a);
+    ark_step_kernel<DIM, Real, SPLIT, VISC, TX, TY, PHIA, NA><<<grid, C::NT, C::SMEM_BYTES, s>>>(a);
     return cudaGetLastError();
 }
 
-template <int DIM, typename Real, bool SPLIT, bool VISC, int TX, int TY, bool PHIA = false>
+template <int DIM, typename Real, bool SPLIT, bool VISC, int TX, int TY, bool PHIA = false, bool NA = false>
 StepKernelInfo step_info()
 {
     using C = StepCfg<DIM, Real, SPLIT, VISC, TX, TY, PHIA>;
     StepKernelInfo k;
-    k.launch = &launch_step_impl<DIM, Real, SPLIT, VISC, TX, TY, PHIA>;
+    k.launch = &launch_step_impl<DIM, Real, SPLIT, VISC, TX, TY, PHIA, NA>;
     k.tx = TX;
     k.ty = TY;
     k.threads = C::NT;

@@ -116,3 +116,25 @@ def test_non_finite_parameters_rejected(ark, field):
         setattr(p, field, inf if field != "K" else float("nan"))
     h = ark._H()
     assert ark.ark_create(ctypes.byref(p), None, ctypes.byref(h)) == ark.ARK_ERR_INVALID_ARG
+
+
+def test_equation_of_state_law_validated(ark):
+    """The law selector and the covolume are checked before any device work;
+    the combinations this build does not implement are refused as such."""
+    from paper_1903_09043_gb300 import inputs as I
+    h = ark._H()
+    for law, b, status in ((2, 0.0, ark.ARK_ERR_INVALID_ARG),                       # unknown law
+                           (ark.ARK_EOS_STIFFENED_GAS, 0.2, ark.ARK_ERR_INVALID_ARG),   # covolume without its law
+                           (ark.ARK_EOS_NOBLE_ABEL, -0.1, ark.ARK_ERR_INVALID_ARG),
+                           (ark.ARK_EOS_NOBLE_ABEL, float("inf"), ark.ARK_ERR_INVALID_ARG)):
+        p = _params(ark)
+        p.eos.law, p.eos.b = law, b
+        assert ark.ark_create(ctypes.byref(p), None, ctypes.byref(h)) == status, (law, b)
+    pp, _ = I.periodic_potential_state(2, (8, 8))
+    p = ark.params_from_problem(pp.replace(b=0.1), ark.ARK_F64)
+    assert p.eos.law == ark.ARK_EOS_NOBLE_ABEL
+    assert ark.ark_create(ctypes.byref(p), None, ctypes.byref(h)) == ark.ARK_ERR_UNSUPPORTED
+    sp, _ = I.stratified_random(2, (8, 8), b=0.1)
+    p = ark.params_from_problem(sp, ark.ARK_F64)
+    fake = ctypes.c_void_p(16)
+    assert ark.ark_compute_dt_noalloc(ctypes.byref(p), fake, fake, None) == ark.ARK_ERR_UNSUPPORTED

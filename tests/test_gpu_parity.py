@@ -719,3 +719,51 @@ def test_stiffened_liquid_column_at_rest_under_tension():
     _, ds = gpu_run(prob, U, 1000, precision="f32split")
     assert ds["max_speed"] < 1e-10
     assert ds["status"] == 0
+
+
+# --------------------------------------------------------------------------
+# Noble-Abel stiffened gas (ARK_EOS_NOBLE_ABEL, covolume b)
+# --------------------------------------------------------------------------
+def _na_periodic():
+    prob, U = I.random_periodic(3, (17, 9, 13), seed=6, mu=0.02, kappa=0.03)
+    return prob.replace(b=0.3), U
+
+
+NOBLE_ABEL_CASES = {
+    "2d_column_reflect": lambda: I.atmosphere((37, 29), p_inf=0.5, b=0.3),
+    "2d_strat_noslip_visc_three_tiles": lambda: I.stratified_random(2, (300, 12), mu=0.01, kappa=0.02, p_inf=0.2, b=0.2),
+    "2d_shock_tube_x": lambda: I.sod(64, axis=0, p_inf=0.3, b=0.4),
+    "2d_shock_tube_y": lambda: I.sod(64, axis=1, p_inf=0.3, b=0.4),
+    "3d_strat_noslip_visc_multi_tile": lambda: I.stratified_random(3, (35, 33, 12), mu=0.005, kappa=0.01, b=0.25),
+    "3d_strat_reflect": lambda: I.stratified_random(3, (19, 6, 8), walls=I.REFLECT_HYDRO, p_inf=0.3, b=0.2),
+    "3d_periodic_visc": _na_periodic,
+}
+
+
+@pytest.mark.parametrize("case", sorted(NOBLE_ABEL_CASES))
+@pytest.mark.parametrize("precision", ["f64", "f32", "f32split"])
+def test_noble_abel_matches_oracle(case, precision):
+    """The second equation of state on the device, every form, against the
+    oracle's law: FP64 within 1e-12, the FP32 forms within their budget."""
+    prob, U = NOBLE_ABEL_CASES[case]()
+    assert prob.b > 0.0
+    n = 20
+    ref, t_ref, dts = O.run(prob, U, n, return_dt=True)
+    V, d = gpu_run(prob, U, n, precision=precision)
+    errs = field_errors(prob, V, ref)
+    assert max(errs) <= (F64_TOL if precision == "f64" else n * F32_STEP_TOL), errs
+    assert d["status"] == 0
+    assert d["dt"] == pytest.approx(dts[-1], rel=1e-13 if precision == "f64" else 1e-5)
+
+
+@pytest.mark.parametrize("precision", ["f64", "f32split"])
+def test_noble_abel_columns_at_rest_on_gpu(precision):
+    """Noble-Abel columns built by Eq. 18 with the law's density stay at rest:
+    an isothermal column between reflective walls and a conducting polytrope
+    between fixed-temperature walls (FP64 to round-off; the split form, with
+    its base state and wall balance in deviation form, to FP32 resolution)."""
+    for prob, U in (I.atmosphere((64, 64), p_inf=0.5, b=0.3),
+                    I.stratified_random(3, (24, 20, 32), amp=0.0, mu=0.01, kappa=0.02, p_inf=0.2, b=0.2)):
+        V, d = gpu_run(prob, U, 500, precision=precision)
+        assert d["status"] == 0
+        assert d["max_speed"] < (1e-12 if precision == "f64" else 1e-9), d["max_speed"]
