@@ -62,7 +62,15 @@ enum {
     ARK_BC_NOSLIP_FIXED_T = 2, /* no-slip wall (all velocity components mirrored with
                                   sign flip) at a fixed temperature T_wall: ghost
                                   T = 2 T_wall - T_mirror; p, rho as above (Sec. 4.5) */
-    ARK_BC_OUTFLOW = 3         /* zero-gradient copy of (rho, u, p)                  */
+    ARK_BC_OUTFLOW = 3,        /* zero-gradient copy of (rho, u, p)                  */
+    ARK_BC_HALO = 4            /* x sides only: the side borders another subdomain of
+                                  a slab decomposition along x (Sec. 3.2: the domain is
+                                  split into subdomains whose ghost zones hold the
+                                  neighbours' cells, exchanged every step).  Its two
+                                  ghost layers are the values last given to
+                                  ark_set_halo (zero before the first); n[0] >= 2.
+                                  Uniform gravity only (no potential array); not in
+                                  ensembles.                                           */
 };
 
 /* Arithmetic of the device state. */
@@ -229,6 +237,35 @@ ark_status ark_time(ark_handle* h, double* t, double* dt);
  * when it is still busy at the limit, ARK_ERR_NONPHYSICAL when the device
  * status word is non-zero, ARK_OK otherwise. */
 ark_status ark_sync(ark_handle* h, double timeout_s);
+
+/* Slab decomposition along x (Sec. 3.2, Implementation: regular domain
+ * decomposition with ghost zones per direction and side).  A subdomain is an
+ * ordinary handle whose inner x sides are ARK_BC_HALO; before each step the
+ * caller moves every subdomain's boundary layers to its neighbours' ghost
+ * layers and gives all subdomains the same dt (the minimum of their
+ * ark_compute_dt, the CFL step of the whole grid).  With FP64 the result
+ * equals the undivided grid's.
+ * Layout of a halo buffer: nf * nv * ny * 2 FP64 values (ny = 1 in 2D; nv
+ * the cells along the last axis), value (f, k, j, l) at
+ * [((f * nv + k) * ny + j) * 2 + l]: field f, plane k of the last axis, row j
+ * of y (3D), layer l counted from the side (l = 0 the layer at the side).
+ *
+ * ark_get_halo: the two cell layers of the current state next to x side
+ * `side` (0: low, 1: high), full values (the split form adds its FP64 base
+ * rows), into `out` (host, or device with on_device = 1; synchronises for a
+ * host buffer).  Any x side may be read.  Needs the state set.
+ * ark_set_halo: the two ghost layers beyond the ARK_BC_HALO side `side`, in
+ * the layout above with l = 0 the ghost layer adjacent to the side: the
+ * neighbour's layers as ark_get_halo returns them from its facing side.  The
+ * values are converted to the state's form (the split form subtracts its
+ * base rows, so it needs its state first) and read by every later ark_step
+ * until the next ark_set_halo.  The caller keeps `in`; a host `in` may be
+ * reused when the call returns.
+ * Errors: ARK_ERR_INVALID_ARG (side not 0/1, that side not ARK_BC_HALO for
+ * ark_set_halo, state not set where needed), ARK_ERR_ALLOC (host staging of
+ * nf * nv * ny * 2 doubles, made on first use), ARK_ERR_CUDA. */
+ark_status ark_get_halo(ark_handle* h, int side, double* out, int on_device);
+ark_status ark_set_halo(ark_handle* h, int side, const double* in, int on_device);
 
 /* Device address and byte size of the current state buffer (read only for
  * the caller; valid until the next ark_step or ark_set_state). */

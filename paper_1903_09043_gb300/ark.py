@@ -35,6 +35,7 @@ ARK_BC_PERIODIC = 0
 ARK_BC_REFLECT_HYDRO = 1
 ARK_BC_NOSLIP_FIXED_T = 2
 ARK_BC_OUTFLOW = 3
+ARK_BC_HALO = 4
 
 ARK_F64 = 0
 ARK_F32 = 1
@@ -94,6 +95,8 @@ _SIGS = {
     "ark_sync": (_st, [_H, ctypes.c_double]),
     "ark_time": (_st, [_H, _dp, _dp]),
     "ark_state_device_ptr": (_st, [_H, ctypes.POINTER(ctypes.c_void_p), ctypes.POINTER(ctypes.c_size_t)]),
+    "ark_get_halo": (_st, [_H, ctypes.c_int, ctypes.c_void_p, ctypes.c_int]),
+    "ark_set_halo": (_st, [_H, ctypes.c_int, ctypes.c_void_p, ctypes.c_int]),
     "ark_launch_shape": (_st, [_H, _ip, _ip, _ip, _ip, _ip]),
     "ark_compute_dt_noalloc": (_st, [ctypes.POINTER(ark_params), ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p]),
     "ark_batch_create": (_st, [ctypes.c_int, ctypes.POINTER(ark_params), ctypes.c_void_p, ctypes.POINTER(_H)]),
@@ -124,6 +127,8 @@ ark_diagnostics = _lib.ark_diagnostics
 ark_sync = _lib.ark_sync
 ark_time = _lib.ark_time
 ark_state_device_ptr = _lib.ark_state_device_ptr
+ark_get_halo = _lib.ark_get_halo
+ark_set_halo = _lib.ark_set_halo
 ark_launch_shape = _lib.ark_launch_shape
 ark_compute_dt_noalloc = _lib.ark_compute_dt_noalloc
 ark_last_error = _lib.ark_last_error
@@ -250,6 +255,24 @@ class Solver:
         v = [ctypes.c_int(0) for _ in range(5)]
         self._check(ark_launch_shape(self.h, *[ctypes.byref(x) for x in v]), "ark_launch_shape")
         return dict(zip(("tx", "ty", "planes", "threads", "blocks"), [x.value for x in v]))
+
+    def halo_shape(self):
+        """Shape of a halo buffer: (fields, planes of the last axis, rows of y (1 in 2D), 2 layers)."""
+        p = self.prob
+        return (p.nfields, p.n[p.dim - 1], p.n[1] if p.dim == 3 else 1, 2)
+
+    def get_halo(self, side: int, out=None):
+        """The two cell layers next to x side ``side`` (0 low, 1 high), layer 0 at the side."""
+        if out is None:
+            out = np.empty(self.halo_shape(), dtype=np.float64)
+        addr, dev = _ptr(out)
+        self._check(ark_get_halo(self.h, int(side), ctypes.c_void_p(addr), dev), "ark_get_halo")
+        return out
+
+    def set_halo(self, side: int, layers) -> None:
+        """Ghost layers beyond the ARK_BC_HALO side ``side`` (layer 0 adjacent to the side)."""
+        addr, dev = _ptr(layers)
+        self._check(ark_set_halo(self.h, int(side), ctypes.c_void_p(addr), dev), "ark_set_halo")
 
     def state_device_ptr(self):
         p = ctypes.c_void_p()

@@ -63,6 +63,8 @@ ark::StepArgs ark::base_args(const ark_handle* h)
     a.energy_form = p.energy_form;
     a.work_per_block = h->work_per_block;
     a.phiA = h->phiA;
+    a.halo[0] = h->halo[0];
+    a.halo[1] = h->halo[1];
     a.planes = h->planes;
     a.tiles_x = h->tiles_x;
     a.tiles_y = h->tiles_y;
@@ -96,7 +98,13 @@ ark_status ark::validate_params(const ark_params* p, std::string& msg)
         if (!(p->grid.hi[d] > p->grid.lo[d])) { msg = "grid.hi must exceed grid.lo"; return ARK_ERR_INVALID_ARG; }
         for (int s = 0; s < 2; ++s) {
             const int bc = s ? p->bc.hi[d] : p->bc.lo[d];
-            if (bc < ARK_BC_PERIODIC || bc > ARK_BC_OUTFLOW) { msg = "unknown boundary condition"; return ARK_ERR_INVALID_ARG; }
+            if (bc < ARK_BC_PERIODIC || bc > ARK_BC_HALO) { msg = "unknown boundary condition"; return ARK_ERR_INVALID_ARG; }
+            if (bc == ARK_BC_HALO && d != 0) {
+                msg = "ARK_BC_HALO borders a neighbouring slab along x only"; return ARK_ERR_INVALID_ARG;
+            }
+            if (bc == ARK_BC_HALO && p->gravity.phi) {
+                msg = "ARK_BC_HALO takes uniform gravity only (no potential array)"; return ARK_ERR_UNSUPPORTED;
+            }
             if (bc != ARK_BC_PERIODIC && p->grid.n[d] < 2) { msg = "walls and outflow need n >= 2 along their axis"; return ARK_ERR_INVALID_ARG; }
             if (bc == ARK_BC_NOSLIP_FIXED_T && !((s ? p->bc.T_hi[d] : p->bc.T_lo[d]) > 0.0)) { msg = "wall temperature must be > 0"; return ARK_ERR_INVALID_ARG; }
             if (bc == ARK_BC_NOSLIP_FIXED_T && p->precision == ARK_F32_SPLIT && d != dim - 1) {
@@ -177,6 +185,12 @@ bool ensure_stage(ark_handle* h, size_t bytes)
         return false;
     }
     return true;
+}
+
+// Values of one halo buffer: nf fields x nv planes x ny rows x 2 layers.
+size_t halo_elems(const ark_handle* h)
+{
+    return (size_t)h->nf * nv_of(h) * (h->dim == 3 ? h->p.grid.n[1] : 1) * 2;
 }
 
 void choose_launch(ark_handle* h, int nsm)
@@ -309,6 +323,17 @@ ark_status ark_create(const ark_params* p, void* cuda_stream, ark_handle** out)
         }
         h->p.gravity.phi = nullptr;   // the caller's array is not referenced after ark_create
     }
+    for (int side = 0; side < 2; ++side) {   // ghost layers of slab boundaries, zero until set
+        if ((side ? p->bc.hi[0] : p->bc.lo[0]) != ARK_BC_HALO) continue;
+        const size_t hb = halo_elems(h) * h->esz;
+        if (cudaMalloc(&h->halo[side], hb) != cudaSuccess) {
+            cudaGetLastError();
+            ark_destroy(h);
+            return ARK_ERR_ALLOC;
+        }
+        e = cudaMemsetAsync(h->halo[side], 0, hb, h->stream);
+        if (e != cudaSuccess) { st = cuda_fail(h, e, "cudaMemsetAsync"); ark_destroy(h); return st; }
+    }
     char* c = (char*)h->ctrl;
     h->smax = (unsigned long long*)c;              // 3 slots
     h->status = (unsigned int*)(c + 32);
@@ -335,6 +360,9 @@ ark_status ark_destroy(ark_handle* h)
     cudaFree(h->stage);
     cudaFree(h->phiA);
     cudaFreeHost(h->status_host);
+    cudaFree(h->halo[0]);
+    cudaFree(h->halo[1]);
+    cudaFree(h->halo_stage);
     delete h;
     return ARK_OK;
 }
@@ -542,6 +570,50 @@ ark_status ark_sync(ark_handle* h, double timeout_s)
     st = wait("status read still pending");
     if (st != ARK_OK) return st;
     if (*h->status_host) return fail(h, ARK_ERR_NONPHYSICAL, "device reported a nonphysical state");
+    return ARK_OK;
+}
+
+ark_status ark_get_halo(ark_handle* h, int side, double* out, int on_device)
+{
+    if (!h || !out || (side != 0 && side != 1)) return fail(h, ARK_ERR_INVALID_ARG, "null argument or side not 0/1");
+    if (!h->state_set) return fail(h, ARK_ERR_INVALID_ARG, "state not set");
+    if (h->p.grid.n[0] < 2) return fail(h, ARK_ERR_INVALID_ARG, "two layers need n[0] >= 2");
+    const size_t bytes = halo_elems(h) * sizeof(double);
+    double* dst = out;
+    if (!on_device) {
+        if (!h->halo_stage && cudaMalloc((void**)&h->halo_stage, bytes) != cudaSuccess) {
+            cudaGetLastError();
+            return fail(h, ARK_ERR_ALLOC, "halo staging buffer");
+        }
+        dst = h->halo_stage;
+    }
+    const ark::StepArgs a = base_args(h);
+    ARK_CUDA(h, ark::launch_halo_get(a, h->prec, side, h->U[h->cur], dst, h->stream));
+    if (!on_device) {
+        ARK_CUDA(h, cudaMemcpyAsync(out, dst, bytes, cudaMemcpyDeviceToHost, h->stream));
+        ARK_CUDA(h, cudaStreamSynchronize(h->stream));
+    }
+    return ARK_OK;
+}
+
+ark_status ark_set_halo(ark_handle* h, int side, const double* in, int on_device)
+{
+    if (!h || !in || (side != 0 && side != 1)) return fail(h, ARK_ERR_INVALID_ARG, "null argument or side not 0/1");
+    if (!h->halo[side]) return fail(h, ARK_ERR_INVALID_ARG, "that x side is not ARK_BC_HALO");
+    if (h->prec == ARK_F32_SPLIT && !h->state_set) return fail(h, ARK_ERR_INVALID_ARG, "the split form needs its state (base rows) first");
+    const size_t bytes = halo_elems(h) * sizeof(double);
+    const double* src = in;
+    if (!on_device) {
+        if (!h->halo_stage && cudaMalloc((void**)&h->halo_stage, bytes) != cudaSuccess) {
+            cudaGetLastError();
+            return fail(h, ARK_ERR_ALLOC, "halo staging buffer");
+        }
+        ARK_CUDA(h, cudaMemcpyAsync(h->halo_stage, in, bytes, cudaMemcpyHostToDevice, h->stream));
+        src = h->halo_stage;
+    }
+    const ark::StepArgs a = base_args(h);
+    ARK_CUDA(h, ark::launch_halo_set(a, h->prec, src, h->halo[side], h->stream));
+    if (!on_device) ARK_CUDA(h, cudaStreamSynchronize(h->stream));   // the caller may reuse `in`
     return ARK_OK;
 }
 

@@ -85,6 +85,58 @@ __global__ void __launch_bounds__(AUX_THREADS) convert_out_kernel(const StepArgs
     }
 }
 
+// Halo layers of a slab decomposition along x.  Element e of the FP64 buffer
+// [NF][nv][ny][2] is field f, plane k, row j, layer l (l = 0 at the side).
+__device__ __forceinline__ void halo_decode(const StepArgs& a, int D, long long e, int& f, int& l, int& j, int& k)
+{
+    const int nv = a.n[D - 1], ny = D == 3 ? a.n[1] : 1;
+    const long long per = (long long)nv * ny * 2;
+    f = (int)(e / per);
+    const long long r = e - (long long)f * per;
+    l = (int)(r & 1);
+    const long long jk = r >> 1;
+    j = (int)(jk % ny);
+    k = (int)(jk / ny);
+}
+
+template <int D, typename Real, bool SPLIT>
+__global__ void __launch_bounds__(AUX_THREADS) halo_get_kernel(const StepArgs a, int side, const Real* __restrict__ U,
+                                                                 double* __restrict__ out)
+{
+    const int nv = a.n[D - 1], nx = a.n[0], ny = D == 3 ? a.n[1] : 1;
+    const long long total = (long long)(D + 2) * nv * ny * 2;
+    for (long long e = blockIdx.x * (long long)blockDim.x + threadIdx.x; e < total; e += (long long)gridDim.x * blockDim.x) {
+        int f, l, j, k;
+        halo_decode(a, D, e, f, l, j, k);
+        const int x = side == 0 ? l : nx - 1 - l;
+        const long long idx = x + (long long)nx * (j + (long long)ny * k);
+        double v = double(U[f * a.ncell + idx]);
+        if constexpr (SPLIT) {   // deviations back to full values with the FP64 base row
+            if (f == 0) v += a.base64[0 * (nv + 4) + k + 2];
+            if (f == D + 1) v += a.base64[2 * (nv + 4) + k + 2];
+        }
+        out[e] = v;
+    }
+}
+
+template <int D, typename Real, bool SPLIT>
+__global__ void __launch_bounds__(AUX_THREADS) halo_set_kernel(const StepArgs a, const double* __restrict__ in,
+                                                                 Real* __restrict__ H)
+{
+    const int nv = a.n[D - 1], ny = D == 3 ? a.n[1] : 1;
+    const long long total = (long long)(D + 2) * nv * ny * 2;
+    for (long long e = blockIdx.x * (long long)blockDim.x + threadIdx.x; e < total; e += (long long)gridDim.x * blockDim.x) {
+        int f, l, j, k;
+        halo_decode(a, D, e, f, l, j, k);
+        double v = in[e];
+        if constexpr (SPLIT) {   // this subdomain's base row
+            if (f == 0) v -= a.base64[0 * (nv + 4) + k + 2];
+            if (f == D + 1) v -= a.base64[2 * (nv + 4) + k + 2];
+        }
+        H[e] = Real(v);
+    }
+}
+
 // One block per row of the last axis; fixed-order tree sums.
 template <int D>
 __global__ void __launch_bounds__(AUX_THREADS) row_means_kernel(const StepArgs a, const double* __restrict__ U,
@@ -238,6 +290,34 @@ cudaError_t launch_wave_rate(const StepArgs& a, int prec, int visc, const void* 
         else { if (visc) ARK_WR(3, float, true, true); else ARK_WR(3, float, true, false); }
     }
 #undef ARK_WR
+    return cudaGetLastError();
+}
+
+cudaError_t launch_halo_get(const StepArgs& a, int prec, int side, const void* U, double* out, cudaStream_t s)
+{
+    const long long total = (long long)(a.dim + 2) * a.n[a.dim - 1] * (a.dim == 3 ? a.n[1] : 1) * 2;
+    const int g = grid_for(total);
+#define ARK_HG(D, R, SP) halo_get_kernel<D, R, SP><<<g, AUX_THREADS, 0, s>>>(a, side, (const R*)U, out)
+    if (a.dim == 2) {
+        if (prec == P_F64) ARK_HG(2, double, false); else if (prec == P_F32) ARK_HG(2, float, false); else ARK_HG(2, float, true);
+    } else {
+        if (prec == P_F64) ARK_HG(3, double, false); else if (prec == P_F32) ARK_HG(3, float, false); else ARK_HG(3, float, true);
+    }
+#undef ARK_HG
+    return cudaGetLastError();
+}
+
+cudaError_t launch_halo_set(const StepArgs& a, int prec, const double* in, void* halo, cudaStream_t s)
+{
+    const long long total = (long long)(a.dim + 2) * a.n[a.dim - 1] * (a.dim == 3 ? a.n[1] : 1) * 2;
+    const int g = grid_for(total);
+#define ARK_HS(D, R, SP) halo_set_kernel<D, R, SP><<<g, AUX_THREADS, 0, s>>>(a, in, (R*)halo)
+    if (a.dim == 2) {
+        if (prec == P_F64) ARK_HS(2, double, false); else if (prec == P_F32) ARK_HS(2, float, false); else ARK_HS(2, float, true);
+    } else {
+        if (prec == P_F64) ARK_HS(3, double, false); else if (prec == P_F32) ARK_HS(3, float, false); else ARK_HS(3, float, true);
+    }
+#undef ARK_HS
     return cudaGetLastError();
 }
 

@@ -16,6 +16,12 @@ cudaError_t launch_wave_rate(const StepArgs& a, int prec, int visc, const void* 
 cudaError_t launch_convert_in(const StepArgs& a, int prec, const double* Uin, void* Uout, cudaStream_t s);
 cudaError_t launch_convert_out(const StepArgs& a, int prec, const void* Uin, double* Uout, cudaStream_t s);
 
+// Slab decomposition along x (BC_HALO): the two cell layers next to x side
+// `side` (0: low, 1: high) as FP64 full values [NF][nv][ny][2], layer 0 at the
+// side; and FP64 ghost layers into a halo buffer of the state's form.
+cudaError_t launch_halo_get(const StepArgs& a, int prec, int side, const void* U, double* out, cudaStream_t s);
+cudaError_t launch_halo_set(const StepArgs& a, int prec, const double* in, void* halo, cudaStream_t s);
+
 // Horizontal means of rho and p of an FP64 full state, one per row of the last axis.
 cudaError_t launch_row_means(const StepArgs& a, const double* U, double* rho_mean, double* p_mean, cudaStream_t s);
 

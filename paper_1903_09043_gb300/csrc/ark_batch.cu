@@ -175,6 +175,7 @@ ark_status ark_batch_create(int count, const ark_params* params, void* cuda_stre
         if (p.precision == ARK_F32) return ARK_ERR_UNSUPPORTED;
         if (p.gravity.phi) return ARK_ERR_UNSUPPORTED;   // ensembles take uniform gravity
         if (p.eos.law != ARK_EOS_STIFFENED_GAS) return ARK_ERR_UNSUPPORTED;   // and the stiffened gas
+        if (p.bc.lo[0] == ARK_BC_HALO || p.bc.hi[0] == ARK_BC_HALO) return ARK_ERR_UNSUPPORTED;   // whole grids
         if ((p.mu > 0.0 || p.kappa > 0.0) != (params[0].mu > 0.0 || params[0].kappa > 0.0)) return ARK_ERR_INVALID_ARG;
     }
     ark_batch* b = new (std::nothrow) ark_batch();

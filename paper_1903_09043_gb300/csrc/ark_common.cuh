@@ -6,7 +6,7 @@
 
 namespace ark {
 
-enum BC : int { BC_PERIODIC = 0, BC_REFLECT = 1, BC_NOSLIP_T = 2, BC_OUTFLOW = 3 };
+enum BC : int { BC_PERIODIC = 0, BC_REFLECT = 1, BC_NOSLIP_T = 2, BC_OUTFLOW = 3, BC_HALO = 4 };
 enum Prec : int { P_F64 = 0, P_F32 = 1, P_F32_SPLIT = 2 };
 enum Status : unsigned { ST_NONPHYS = 1u, ST_LTILDE = 2u, ST_NAN = 4u };
 
@@ -58,6 +58,8 @@ struct StepArgs {
     void* Uout;
     const void* base;       // BaseField tables (F32_SPLIT), else nullptr
     const void* phiA;       // caller-supplied potential at the cell centres (Real, one field), or null
+    const void* halo[2];    // BC_HALO sides of x (low, high): the neighbouring subdomain's two cell
+                            // layers beyond the side, Real [NF][nv][ny][2], layer 1 (adjacent) first
     const double* base64;   // FP64 rho0, p0, W0, Phi per row, rows -2 .. nv + 1 (F32_SPLIT)
     double dt_fixed;        // > 0: fixed step; otherwise cfl / smax[slot_read]
     unsigned long long* smax;  // 3 slots of FP64 bit patterns (max wave rate)

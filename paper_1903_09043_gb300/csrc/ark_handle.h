@@ -20,6 +20,8 @@ struct ark_handle {
     double* stage = nullptr;       // FP64 staging of host states (FP32 forms), nf * N, made on first use
     void* phiA = nullptr;          // caller-supplied potential, N values of the state precision
     std::vector<double> phi_rows;  // F32_SPLIT with a potential array: Phi of rows -2 .. nv + 1
+    void* halo[2] = {nullptr, nullptr};   // ghost layers beyond BC_HALO x sides, state precision [nf][nv][ny][2]
+    double* halo_stage = nullptr;  // FP64 staging of host halo transfers, nf * nv * ny * 2
     void* ctrl = nullptr;          // smax[3] | status | pad | time | dt_last | diag out[16] | partials
     unsigned long long* smax = nullptr;
     unsigned int* status = nullptr;

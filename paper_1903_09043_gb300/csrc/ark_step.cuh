@@ -518,6 +518,23 @@ struct Stepper {
         return c;
     }
 
+    // Ghost layer `layer` (1, 2) beyond a BC_HALO side of x at row gy of plane
+    // gv: a cell of the neighbouring subdomain (Sec. 3.2: ghost zones hold the
+    // neighbours' cells), stored by the caller in the state's form.
+    __device__ Cell<D, Real> load_halo(bool lo, int layer, int gy, int gv, const Row<Real>& w) const
+    {
+        const Real* __restrict__ H = static_cast<const Real*>(a.halo[lo ? 0 : 1]);
+        const long long per = (long long)nv * ny * 2;
+        const long long idx = ((long long)gv * ny + gy) * 2 + (layer - 1);
+        Cell<D, Real> c;
+        c.drho = __ldg(H + idx);
+#pragma unroll
+        for (int d = 0; d < D; ++d) c.m[d] = __ldg(H + (1 + d) * per + idx);
+        c.dW = __ldg(H + (D + 1) * per + idx);
+        prim<D, Real, SPLIT>(c, w, eos);
+        return c;
+    }
+
     // in-plane axis rule (axis 0 = x, axis 1 = y in 3D).  All in-plane
     // ghosts share the row of their plane; for uniform gravity along the last
     // axis dPhi = 0 across in-plane walls, with a Phi array the wall ghost sees
@@ -528,6 +545,7 @@ struct Stepper {
         const bool lo = gx < 0;
         const int bc = lo ? a.bc_lo[0] : a.bc_hi[0];
         if (bc == BC_PERIODIC) return load_in(((gx % nx) + nx) % nx, gy, gv, w);
+        if (bc == BC_HALO) return load_halo(lo, lo ? -gx : gx - nx + 1, gy, gv, w);
         if (bc == BC_OUTFLOW) {
             Cell<D, Real> M = load_in(lo ? 0 : nx - 1, gy, gv, w);
             if constexpr (PHIA) cons_from_prim<D, Real, SPLIT>(M, at(w, gx, gy, gv), eos);
