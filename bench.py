@@ -407,6 +407,13 @@ def batch_path(args, stream, hbm):
     achieved = cells * ALG_BYTES[("f32split", 2)] / (ms * 1e-3) / 1e9
     flops = ALG_FLOPS[(2, all(p.mu > 0 or p.kappa > 0 for p in probs))]
     tflops = cells * flops / (ms * 1e-3) / 1e12
+    wipc = kernel_traffic("batch", "warp_inst_per_cell")
+    issue = None
+    if wipc is not None:
+        gw = wipc * cells / (ms * 1e-3) / 1e9
+        issue = {"achieved": gw, "peak": ISSUE_PEAK_GWARP, "unit": "G warp-instructions/s",
+                 "frac": gw / ISSUE_PEAK_GWARP, "warp_inst_per_cell": wipc,
+                 "peak_kind": "4 issue slots per SM per clock at the maximum SM clock; instructions per cell from ncu"}
     return {"value": cells / (ms * 1e-3), "ms_per_step": ms, "runs": len(runs), "cells": cells, "dtype": "f32",
             "one_at_a_time_value": cells / (ms_one * 1e-3), "one_at_a_time_ms_per_step": ms_one,
             "speedup_vs_one_at_a_time": ms_one / ms, "tile": shape, "tuned": {"tx": tx, "planes": planes},
@@ -414,7 +421,8 @@ def batch_path(args, stream, hbm):
             "roofline": {"bound": "hbm", "achieved": achieved, "peak": hbm, "unit": "GB/s", "frac": achieved / hbm,
                          "alg_bytes_per_cell": ALG_BYTES[("f32split", 2)], "traffic": kernel_traffic("batch"),
                          "alu": {"achieved": tflops, "peak": ALU_PEAK_TFLOPS["f32"], "unit": "TFLOP/s",
-                                 "frac": tflops / ALU_PEAK_TFLOPS["f32"], "alg_flops_per_cell": flops}}}
+                                 "frac": tflops / ALU_PEAK_TFLOPS["f32"], "alg_flops_per_cell": flops},
+                         "issue": issue}}
 
 
 def main():
