@@ -138,3 +138,35 @@ def test_equation_of_state_law_validated(ark):
     p = ark.params_from_problem(sp, ark.ARK_F64)
     fake = ctypes.c_void_p(16)
     assert ark.ark_compute_dt_noalloc(ctypes.byref(p), fake, fake, None) == ark.ARK_ERR_UNSUPPORTED
+
+
+def test_halo_boundary_rules(ark):
+    """ARK_BC_HALO (slab boundaries of a decomposition along x) is checked
+    before any device work: x sides only, n[0] >= 2, uniform gravity only,
+    and not in ensembles."""
+    from paper_1903_09043_gb300 import inputs as I
+    h = ark._H()
+    p = _params(ark)
+    p.bc.lo[0] = p.bc.hi[0] = ark.ARK_BC_HALO
+    p.grid.n[0] = 1
+    assert ark.ark_create(ctypes.byref(p), None, ctypes.byref(h)) == ark.ARK_ERR_INVALID_ARG
+    p = _params(ark)
+    p.bc.lo[1] = ark.ARK_BC_HALO                       # not along the gravity axis
+    assert ark.ark_create(ctypes.byref(p), None, ctypes.byref(h)) == ark.ARK_ERR_INVALID_ARG
+    p = _params(ark)
+    p.bc.lo[0] = ark.ARK_BC_HALO                       # a halo side facing a periodic one
+    assert ark.ark_create(ctypes.byref(p), None, ctypes.byref(h)) == ark.ARK_ERR_INVALID_ARG
+    p = _params(ark)
+    p.bc.lo[0] = 5                                     # beyond the known rules
+    assert ark.ark_create(ctypes.byref(p), None, ctypes.byref(h)) == ark.ARK_ERR_INVALID_ARG
+    tp, _ = I.tilted_atmosphere((16, 12))
+    q = ark.params_from_problem(tp, ark.ARK_F64)
+    q.bc.lo[0] = q.bc.hi[0] = ark.ARK_BC_HALO
+    assert ark.ark_create(ctypes.byref(q), None, ctypes.byref(h)) == ark.ARK_ERR_UNSUPPORTED
+    assert not h.value
+    runs = (ark.ark_params * 2)(_params(ark), _params(ark))
+    runs[1].bc.lo[0] = runs[1].bc.hi[0] = ark.ARK_BC_HALO
+    b = ctypes.c_void_p()
+    assert ark.ark_batch_create(2, runs, None, ctypes.byref(b)) == ark.ARK_ERR_UNSUPPORTED
+    assert ark.ark_get_halo(None, 0, None, 0) == ark.ARK_ERR_INVALID_ARG
+    assert ark.ark_set_halo(None, 0, None, 0) == ark.ARK_ERR_INVALID_ARG
