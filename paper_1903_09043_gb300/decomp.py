@@ -94,13 +94,14 @@ class SlabDecomposition:
 def advance_local(decomp: SlabDecomposition, solvers: Sequence, nsteps: int) -> float:
     """Advance every subdomain of ``decomp`` (solver r on slab r, all in this
     process) by ``nsteps`` steps: halos moved device to device, the time step
-    the minimum of the subdomains' CFL steps.  Returns the last time step."""
+    the minimum of the subdomains' CFL steps.  Returns the last time step.
+    The solvers must share one CUDA stream (the halo buffers are written by
+    one handle's kernels and read by another's, in stream order)."""
     import torch
     dt = 0.0
-    shapes = [s.halo_shape() for s in solvers]
+    out = [(torch.empty(s.halo_shape(), dtype=torch.float64, device="cuda"),
+            torch.empty(s.halo_shape(), dtype=torch.float64, device="cuda")) for s in solvers]
     for _ in range(nsteps):
-        out = [(torch.empty(shapes[r], dtype=torch.float64, device="cuda"),
-                torch.empty(shapes[r], dtype=torch.float64, device="cuda")) for r in range(len(solvers))]
         for r, s in enumerate(solvers):
             s.get_halo(0, out[r][0])
             s.get_halo(1, out[r][1])
