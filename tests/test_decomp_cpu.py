@@ -73,7 +73,16 @@ CASES = {
     "2d_rb_walls_in_y": lambda: I.rayleigh_benard(2, (24, 12), amp=1e-2),
     "2d_shock_tube_outflow_x": lambda: I.sod(30, axis=0),
     "3d_periodic_visc": lambda: I.random_periodic(3, (12, 7, 5), seed=3, mu=0.02, kappa=0.03),
+    "3d_walls_in_y_outflow_x": lambda: _walls_in_y(),
 }
+
+
+def _walls_in_y():
+    prob, U = I.stratified_random(3, (12, 6, 5), mu=0.01, kappa=0.02, walls=I.REFLECT_HYDRO)
+    lo, hi = list(prob.bc_lo), list(prob.bc_hi)
+    lo[0] = hi[0] = I.OUTFLOW
+    lo[1] = hi[1] = I.REFLECT_HYDRO
+    return prob.replace(bc_lo=tuple(lo), bc_hi=tuple(hi)), U
 
 
 def test_slab_bounds_and_sub_problems():
@@ -136,7 +145,8 @@ def _worker(rank, world, port, case, nsteps, q):
 
 
 @pytest.mark.parametrize("case,world", [("2d_periodic_visc", 2), ("2d_rb_walls_in_y", 3),
-                                        ("2d_shock_tube_outflow_x", 3), ("3d_periodic_visc", 2)])
+                                        ("2d_shock_tube_outflow_x", 3), ("3d_periodic_visc", 2),
+                                        ("3d_walls_in_y_outflow_x", 3)])
 def test_gloo_ranks_equal_undivided_grid(case, world):
     import torch.multiprocessing as mp
     ctx = mp.get_context("spawn")

@@ -27,8 +27,20 @@ def _ark():
     return ark
 
 
+def _walls_in_y():
+    """3D layer with reflective walls across y and outflow ends in x (gravity
+    along z): the corner ghosts beyond a slab boundary come from the y wall
+    rule applied to halo cells."""
+    prob, U = I.stratified_random(3, (48, 10, 9), mu=0.01, kappa=0.02, walls=I.REFLECT_HYDRO)
+    lo, hi = list(prob.bc_lo), list(prob.bc_hi)
+    lo[0] = hi[0] = I.OUTFLOW
+    lo[1] = hi[1] = I.REFLECT_HYDRO
+    return prob.replace(bc_lo=tuple(lo), bc_hi=tuple(hi)), U
+
+
 CASES = {
     "2d_rb_three_slabs": (lambda: I.rayleigh_benard(2, (96, 32), amp=1e-2), 3),
+    "3d_walls_in_y_outflow_x": (_walls_in_y, 3),
     "2d_shock_tube_outflow_x": (lambda: I.sod(90, axis=0), 3),
     "3d_strat_noslip_visc": (lambda: I.stratified_random(3, (70, 33, 12), mu=0.005, kappa=0.005), 2),
     "3d_periodic_noble_abel": (lambda: (lambda pu: (pu[0].replace(b=0.3), pu[1]))(
