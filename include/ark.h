@@ -258,8 +258,9 @@ ark_status ark_sync(ark_handle* h, double timeout_s);
  * the layout above with l = 0 the ghost layer adjacent to the side: the
  * neighbour's layers as ark_get_halo returns them from its facing side.  The
  * values are converted to the state's form (the split form subtracts its
- * base rows, so it needs its state first) and read by every later ark_step
- * until the next ark_set_halo.  The caller keeps `in`; a host `in` may be
+ * base rows, so it needs its state first, and ark_set_state, which forms new
+ * base rows, calls for the halos to be set again) and read by every later
+ * ark_step until the next ark_set_halo.  The caller keeps `in`; a host `in` may be
  * reused when the call returns.
  * Errors: ARK_ERR_INVALID_ARG (side not 0/1, that side not ARK_BC_HALO for
  * ark_set_halo, state not set where needed), ARK_ERR_ALLOC (host staging of
