@@ -11,9 +11,10 @@ viscous and heat fluxes, next CFL time step).
 
 Paths timed: ``f32split`` (headline: FP32 state and stencil arithmetic, FP64
 base state) and ``f64`` (FP64 throughout) on that workload; ``f32split_2d``
-on the 2D Rayleigh-Benard layer (8192 x 4096); ``gresho_f32split`` and
-``gresho_f64`` on the inviscid Gresho vortex (8192 x 8192, Sec. 4.2), where
-the step does the fewest operations per byte; and the 256-run ensemble.
+on the 2D Rayleigh-Benard layer (8192 x 4096); ``gresho_f32split``,
+``gresho_f32`` (plain FP32 state) and ``gresho_f64`` on the inviscid Gresho
+vortex (8192 x 8192, Sec. 4.2), where the step does the fewest operations per
+byte; and the 256-run ensemble.
 ``--impl reference`` times the FP64 CPU oracle on slabs of the same workload
 instead.
 
@@ -431,7 +432,7 @@ def main():
     ap.add_argument("--steps", type=int, default=200)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
-    ap.add_argument("--paths", default="f32split,f64,f32split_2d,gresho_f32split,gresho_f64",
+    ap.add_argument("--paths", default="f32split,f64,f32split_2d,gresho_f32split,gresho_f32,gresho_f64",
                     help="comma list of " + ", ".join(PATHS) + "; the first is the headline")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")

@@ -347,7 +347,7 @@ def test_full_size_2d_rb_sampled(precision):
 _GRESHO = {}
 
 
-@pytest.mark.parametrize("precision", ["f64", "f32split"])
+@pytest.mark.parametrize("precision", ["f64", "f32split", "f32"])
 def test_full_size_gresho_8192_two_steps_every_cell(precision):
     """Inviscid Gresho vortex on 8192 x 8192 (the benchmark's HBM roofline
     workload, Sec. 4.2, Ma = 1e-2, its launch shape): two GPU steps with the
