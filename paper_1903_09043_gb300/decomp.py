@@ -124,7 +124,11 @@ class DecomposedSolver:
     ``solver`` is the slab's solver (an :class:`~paper_1903_09043_gb300.ark.Solver`
     on ``decomp.sub_problem(rank)``, or any object with ``get_halo``,
     ``set_halo``, ``halo_shape``, ``compute_dt`` and ``step``).  With the
-    gloo backend halos travel as host arrays, with nccl as device tensors."""
+    gloo backend halos travel as host arrays, with nccl as device tensors.
+    Device halos are written and read on the solver's stream, while NCCL
+    orders its work after torch's current stream, so in device mode the
+    solver's stream is synchronised before a send and the current stream
+    after the receives."""
 
     TAG_FROM_LOW, TAG_FROM_HIGH = 0, 1   # which side of the sender the layers come from
 
@@ -146,6 +150,9 @@ class DecomposedSolver:
             return torch.from_numpy(self.solver.get_halo(side))
         buf = self._buffer()
         self.solver.get_halo(side, buf)
+        sync = getattr(self.solver, "sync", None)
+        if sync is not None:
+            sync()          # the layers are in buf before the collective reads it
         return buf
 
     def exchange(self) -> None:
@@ -166,6 +173,9 @@ class DecomposedSolver:
             recvs.append(dist.irecv(got_hi, self.right, group=self.group, tag=self.TAG_FROM_LOW))
         for w in recvs + sends:
             w.wait()
+        if self.device != "cpu" and recvs:
+            import torch
+            torch.cuda.current_stream().synchronize()   # received layers complete before the solver's stream reads them
         if got_lo is not None:
             self.solver.set_halo(0, got_lo.numpy() if self.device == "cpu" else got_lo)
         if got_hi is not None:
