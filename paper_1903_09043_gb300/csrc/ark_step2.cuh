@@ -33,7 +33,7 @@
 
 namespace ark {
 
-template <int DIM, typename Real, bool SPLIT, bool VISC, int R2X_, int R2Y_, bool PHIA = false>
+template <int DIM, typename Real, bool SPLIT, bool VISC, int R2X_, int R2Y_, bool PHIA = false, bool ENS = false>
 struct Step2Cfg {
     static constexpr int D = DIM, NF = DIM + 2, V = DIM - 1;
     static constexpr int R2X = R2X_, R2Y = R2Y_, NT = R2X * R2Y;
@@ -60,21 +60,24 @@ struct Step2Cfg {
     static constexpr int BRING = 8;                               // base rows kept in shared memory (split form)
     static constexpr size_t O_BASE = ((N_REAL * sizeof(Real) + 15) / 16) * 16;
     static constexpr size_t O_RED = O_BASE + (SPLIT ? BRING * BSTRIDE * sizeof(float) : 0);
-    // Plain FP32 in 2D: each thread copies its own column three planes ahead into
-    // a shared ring of 4 planes (cp.async), which hides the load latency of a
-    // 2D block's short planes (about 1 us each).  Measured on 8192 x 8192
-    // (inviscid) 81 -> 95 G cell-updates/s, the viscous layer unchanged; the
-    // split form ran slower with the ring and keeps the one-plane register
-    // prefetch, as does 3D, where a plane takes ten times longer.
-    static constexpr bool RING = DIM == 2 && !SPLIT && !PHIA;
+    // 2D: each thread copies its own column three planes ahead into a shared
+    // ring of 4 planes (cp.async), which hides the load latency of a 2D block's
+    // short planes (about 1 us each); in the split form the first BSTRIDE
+    // threads copy the base row each plane needs in the same group, so no
+    // thread waits on a load before a barrier.  The viscous split step of one
+    // grid (ENS false: not an ensemble item) keeps the one-plane register
+    // prefetch, which its longer planes hide and which measured faster there,
+    // as does 3D, where a plane takes ten times longer.
+    static constexpr bool RING = DIM == 2 && !PHIA && !(SPLIT && VISC && !ENS);
     static constexpr size_t O_RING = O_RED + NT * sizeof(double) + 4 * sizeof(double);
     static constexpr size_t SMEM_BYTES = O_RING + (RING ? 4 * NF * NT * sizeof(Real) : 0);
     static_assert(NT % 32 == 0 && NT <= 1024, "block must be whole warps");
 };
 
 // Four consecutive base-table entries of one row.  The block keeps the rows
-// it is using in a shared ring of BRING rows (slot r & (BRING - 1)), filled one
-// plane ahead, so each read is a 16-byte shared broadcast.
+// it is using in a shared ring of BRING rows (slot r & (BRING - 1)), filled
+// ahead of use (one plane ahead in 3D, with the state ring's copies in 2D), so
+// each read is a 16-byte shared broadcast.
 struct Base4 {
     float x, y, z, w;
 };
@@ -136,11 +139,12 @@ __device__ __forceinline__ void flux_update_n(float* c, const float* a, float s,
     }
 }
 
-template <int DIM, typename Real, bool SPLIT, bool VISC, int R2X, int R2Y, bool PHIA = false, bool NA = false>
+template <int DIM, typename Real, bool SPLIT, bool VISC, int R2X, int R2Y, bool PHIA = false, bool NA = false,
+          bool ENS = false>
 __device__ __forceinline__ void step_block2(const StepArgs& a, const int tile, const int z0, const int z1, const bool lead,
                                             unsigned char* smem_raw)
 {
-    using C = Step2Cfg<DIM, Real, SPLIT, VISC, R2X, R2Y, PHIA>;
+    using C = Step2Cfg<DIM, Real, SPLIT, VISC, R2X, R2Y, PHIA, ENS>;
     constexpr int D = DIM, NF = DIM + 2, V = DIM - 1, NT = C::NT, TX = C::TX, TY = C::TY;
     static_assert(!SPLIT || sizeof(Real) == 4, "the split form stores FP32 deviations");
     Real* sm = reinterpret_cast<Real*>(smem_raw);
@@ -225,6 +229,12 @@ __device__ __forceinline__ void step_block2(const StepArgs& a, const int tile, c
                 const unsigned idx = cidx + plane_cells * (unsigned)p;
 #pragma unroll
                 for (int k = 0; k < NF; ++k) cp_async4(ringp + ((p & 3) * NF + k) * NT, Uin + k * N + idx);
+            }
+            // base row p + 1, read from plane p + 1 on (the ring's 8 rows hold
+            // rows p - 3 .. p + 4 while the copy is in flight)
+            if constexpr (SPLIT) {
+                if (t < BSTRIDE && p + 1 <= nv + 1)
+                    cp_async4(bring + ((p + 1) & (C::BRING - 1)) * BSTRIDE + t, Bt + base_index(t, p + 1));
             }
             cp_async_commit();
         } else {
@@ -589,7 +599,7 @@ __device__ __forceinline__ void step_block2(const StepArgs& a, const int tile, c
         // ================= H2 =================
         // next base row into the ring (read from the next plane on)
         float bnext = 0.f;
-        if constexpr (SPLIT) {
+        if constexpr (SPLIT && !C::RING) {
             if (t < BSTRIDE && (STEADY || f + 1 <= nv + 1)) bnext = __ldg(Bt + base_index(t, f + 1));
         }
         // own +x / +y acoustic faces of plane f
@@ -717,7 +727,7 @@ __device__ __forceinline__ void step_block2(const StepArgs& a, const int tile, c
             if (ocol && (sh != sh || p != p)) status |= ST_NAN;
             if (ocol && (!(rho > Real(0)) || !(p > Real(0)))) status |= ST_NONPHYS;
         }
-        if constexpr (SPLIT) {
+        if constexpr (SPLIT && !C::RING) {
             if (t < BSTRIDE && (STEADY || f + 1 <= nv + 1)) bring[((f + 1) & (BR - 1)) * BSTRIDE + t] = bnext;
         }
         __syncthreads();
@@ -816,7 +826,7 @@ ark_batch2_kernel(const StepArgs* __restrict__ runs, const BatchItem* __restrict
         const BatchItem w = items[it];
         const StepArgs& r = runs[w.run];
         const int z0 = w.chunk * r.planes;
-        step_block2<DIM, Real, SPLIT, VISC, R2X, R2Y>(r, w.tile, z0, min(z0 + r.planes, r.n[DIM - 1]),
+        step_block2<DIM, Real, SPLIT, VISC, R2X, R2Y, false, false, true>(r, w.tile, z0, min(z0 + r.planes, r.n[DIM - 1]),
                                                       w.tile == 0 && w.chunk == 0, smem_raw);
     }
 }

@@ -42,7 +42,7 @@ StepKernelInfo step2_info()
 template <typename Real, bool SPLIT, bool VISC, int R2X>
 BatchKernelInfo batch2_info()
 {
-    using C = Step2Cfg<2, Real, SPLIT, VISC, R2X, 1>;
+    using C = Step2Cfg<2, Real, SPLIT, VISC, R2X, 1, false, true>;
     BatchKernelInfo k;
     k.func = reinterpret_cast<const void*>(&ark_batch2_kernel<2, Real, SPLIT, VISC, R2X, 1>);
     k.tx = C::TX;
