@@ -38,6 +38,19 @@ StepKernelInfo step_info()
     int b = (int)(per_sm / (C::SMEM_BYTES + 1024));
     if (b < 1) b = 1;
     if (b * C::NT > 2048) b = 2048 / C::NT;
+    // Registers can leave room for fewer blocks than shared memory does (the 2D
+    // FP64 kernel: two blocks' rings fit, one block's registers): take the
+    // runtime's count when no earlier error is pending, else the estimate.
+    if (cudaPeekAtLastError() == cudaSuccess) {
+        const auto f = ark_step_kernel<DIM, Real, SPLIT, VISC, TX, TY, PHIA, NA>;
+        int occ = 0;
+        if (cudaFuncSetAttribute(f, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)C::SMEM_BYTES) == cudaSuccess &&
+            cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, f, C::NT, C::SMEM_BYTES) == cudaSuccess) {
+            if (occ >= 1) b = occ;
+        } else {
+            cudaGetLastError();   // the query's own error; nothing else was pending
+        }
+    }
     k.blocks_per_sm = b;
     k.balanced = true;
     return k;
