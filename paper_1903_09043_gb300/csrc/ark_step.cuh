@@ -1190,7 +1190,7 @@ __device__ __forceinline__ void step_block(const StepArgs& a, const int tile, co
 // tile-major list of (tile, plane) units, as one run of planes per tile it
 // touches (W = work_per_block).
 template <int DIM, typename Real, bool SPLIT, bool VISC, int TX, int TY, bool PHIA = false, bool NA = false>
-__global__ void __launch_bounds__(TX * TY, sizeof(Real) == 8 ? 1 : 2)
+__global__ void __launch_bounds__(TX * TY, sizeof(Real) == 8 ? (DIM == 2 ? 2 : 1) : 2)
 ark_step_kernel(const __grid_constant__ StepArgs a)
 {
     extern __shared__ __align__(16) unsigned char smem_raw[];
