@@ -19,7 +19,9 @@ exchange:
   ``torch.distributed`` process group: every step each rank sends the layers
   at its x sides to the neighbours on those sides, takes theirs as its ghost
   layers, and joins an allreduce-min of the time step.  Halos travel as host
-  arrays (gloo) or device tensors (nccl).
+  arrays (gloo) or device tensors (nccl).  Whole-grid diagnostics are the
+  slabs' own, combined by allreduce (sums, maxima, minima);
+* :func:`combine_diagnostics` -- the same combination for slabs in one process.
 
 Only uniform gravity along the last axis is decomposed (the slab boundary is
 then free of potential jumps), as the library requires for ``ARK_BC_HALO``.
@@ -33,6 +35,11 @@ import numpy as np
 from .inputs import PERIODIC
 
 HALO = 4   # ARK_BC_HALO: the x side borders a neighbouring slab
+
+# diagnostics that add up over slabs (integrals over the cells); the mean |v|
+# of the last axis adds up once weighted by the slab's cells
+SUMMED = ("mass", "mom_x", "mom_y", "mom_z", "energy", "kinetic")
+STATUS_BITS = (1, 2, 4)   # nonphysical rho/p, L~ <= 0, NaN
 
 
 def slab_bounds(nx: int, parts: int) -> List[Tuple[int, int]]:
@@ -89,6 +96,31 @@ class SlabDecomposition:
 
     def join(self, parts: Sequence[np.ndarray]) -> np.ndarray:
         return np.concatenate(list(parts), axis=-1)
+
+    def cells(self, r: int) -> int:
+        """Cells of slab r."""
+        i0, i1 = self.bounds[r]
+        return (i1 - i0) * int(np.prod(self.prob.n[1:]))
+
+
+def combine_diagnostics(parts: Sequence[dict], cells: Sequence[int]) -> dict:
+    """Whole-grid diagnostics from the slabs' own (``parts[r]`` of a slab of
+    ``cells[r]`` cells, keys as ``Solver.diagnostics``): integrals summed, the
+    mean |v| weighted by cells, the largest speed, the smallest rho and p,
+    status bits or-ed; time, step and dt are the first slab's (all slabs
+    advance together)."""
+    out = dict(parts[0])
+    for k in SUMMED:
+        out[k] = sum(d[k] for d in parts)
+    out["mean_abs_v_last"] = sum(d["mean_abs_v_last"] * n for d, n in zip(parts, cells)) / sum(cells)
+    out["max_speed"] = max(d["max_speed"] for d in parts)
+    out["min_rho"] = min(d["min_rho"] for d in parts)
+    out["min_p"] = min(d["min_p"] for d in parts)
+    status = 0
+    for d in parts:
+        status |= int(d.get("status", 0))
+    out["status"] = status
+    return out
 
 
 def advance_local(decomp: SlabDecomposition, solvers: Sequence, nsteps: int) -> float:
@@ -180,6 +212,31 @@ class DecomposedSolver:
             self.solver.set_halo(0, got_lo.numpy() if self.device == "cpu" else got_lo)
         if got_hi is not None:
             self.solver.set_halo(1, got_hi.numpy() if self.device == "cpu" else got_hi)
+
+    def global_diagnostics(self) -> dict:
+        """Diagnostics of the whole grid, the same on every rank (one allreduce
+        each for the sums, the maxima and the minima)."""
+        import torch
+        import torch.distributed as dist
+        d = dict(self.solver.diagnostics(check=False))
+        n = self.decomp.cells(self.rank)
+        total = sum(self.decomp.cells(r) for r in range(self.decomp.parts))
+        st = int(d.get("status", 0))
+        sums = torch.tensor([d[k] for k in SUMMED] + [d["mean_abs_v_last"] * n], dtype=torch.float64, device=self.device)
+        maxs = torch.tensor([d["max_speed"]] + [1.0 if st & b else 0.0 for b in STATUS_BITS], dtype=torch.float64,
+                            device=self.device)
+        mins = torch.tensor([d["min_rho"], d["min_p"]], dtype=torch.float64, device=self.device)
+        dist.all_reduce(sums, op=dist.ReduceOp.SUM, group=self.group)
+        dist.all_reduce(maxs, op=dist.ReduceOp.MAX, group=self.group)
+        dist.all_reduce(mins, op=dist.ReduceOp.MIN, group=self.group)
+        sums, maxs, mins = sums.tolist(), maxs.tolist(), mins.tolist()
+        for i, k in enumerate(SUMMED):
+            d[k] = sums[i]
+        d["mean_abs_v_last"] = sums[len(SUMMED)] / total
+        d["max_speed"] = maxs[0]
+        d["status"] = sum(b for b, on in zip(STATUS_BITS, maxs[1:]) if on > 0.5)
+        d["min_rho"], d["min_p"] = mins
+        return d
 
     def global_dt(self) -> float:
         """Minimum of the ranks' CFL time steps: the CFL step of the whole grid."""

@@ -16,7 +16,7 @@ import pytest
 
 import oracle as O
 from paper_1903_09043_gb300 import inputs as I
-from paper_1903_09043_gb300.decomp import HALO, DecomposedSolver, SlabDecomposition, slab_bounds
+from paper_1903_09043_gb300.decomp import HALO, DecomposedSolver, SlabDecomposition, combine_diagnostics, slab_bounds
 from parity import field_errors
 
 TOL = 1e-14
@@ -50,6 +50,11 @@ class OracleSlab:
 
     def compute_dt(self):
         return O.dt(self._plain(), self.U)
+
+    def diagnostics(self, check=False):
+        d = O.diagnostics(self._plain(), self.U)
+        d.update(t=0.0, step=0, dt=0.0, status=0)
+        return d
 
     def step(self, n, dt):
         p = self._plain()
@@ -121,6 +126,16 @@ def test_local_stand_in_equals_undivided_oracle():
             s.step(1, dt)
     ref, _ = O.run(prob, U, 4)
     assert max(field_errors(prob, dec.join([s.U for s in slabs]), ref)) <= TOL
+    _check_diagnostics(combine_diagnostics([s.diagnostics() for s in slabs], [dec.cells(r) for r in range(3)]),
+                       O.diagnostics(prob, ref))
+
+
+def _check_diagnostics(got, want):
+    """Whole-grid diagnostics from the slabs against the undivided grid's
+    (sums in another order, and each slab's cell size formed from its own box)."""
+    for k, v in want.items():
+        scale = max(abs(v), abs(want["mass"]) if k.startswith("mom") else abs(v), 1e-300)
+        assert abs(got[k] - v) <= 1e-12 * scale, (k, got[k], v)
 
 
 def _free_port():
@@ -138,8 +153,9 @@ def _worker(rank, world, port, case, nsteps, q):
         prob, U = CASES[case]()
         dec = SlabDecomposition(prob, world)
         slab = OracleSlab(dec.sub_problem(rank), dec.split(U)[rank])
-        dt = DecomposedSolver(dec, rank, slab).step(nsteps)
-        q.put((rank, slab.U, dt))
+        ds = DecomposedSolver(dec, rank, slab)
+        dt = ds.step(nsteps)
+        q.put((rank, slab.U, dt, ds.global_diagnostics()))
     finally:
         dist.destroy_process_group()
 
@@ -155,7 +171,7 @@ def test_gloo_ranks_equal_undivided_grid(case, world):
     procs = [ctx.Process(target=_worker, args=(r, world, port, case, 5, q)) for r in range(world)]
     for p in procs:
         p.start()
-    got = dict((r, (V, dt)) for r, V, dt in (q.get(timeout=120) for _ in range(world)))
+    got = dict((r, (V, dt, dg)) for r, V, dt, dg in (q.get(timeout=120) for _ in range(world)))
     for p in procs:
         p.join(60)
         assert p.exitcode == 0
@@ -164,3 +180,22 @@ def test_gloo_ranks_equal_undivided_grid(case, world):
     ref, t, dts = O.run(prob, U, 5, return_dt=True)
     assert max(field_errors(prob, dec.join([got[r][0] for r in range(world)]), ref)) <= TOL
     assert all(got[r][1] == pytest.approx(dts[-1], rel=1e-14) for r in range(world))
+    want = O.diagnostics(prob, ref)
+    for r in range(world):   # every rank holds the whole grid's diagnostics
+        _check_diagnostics(got[r][2], want)
+
+
+def test_combined_diagnostics_of_uneven_slabs():
+    """Five slabs of 5, 5, 5, 5 and 4 columns: the integrals add up, the mean
+    |v| is weighted by each slab's cells, extremes are the grid's."""
+    prob, U = I.rayleigh_benard(2, (24, 12), amp=1e-2)
+    dec = SlabDecomposition(prob, 5)
+    assert sorted({dec.cells(r) for r in range(5)}) == [4 * 12, 5 * 12]
+    slabs = [OracleSlab(dec.sub_problem(r), V) for r, V in enumerate(dec.split(U))]
+    parts = [s.diagnostics() for s in slabs]
+    got = combine_diagnostics(parts, [dec.cells(r) for r in range(5)])
+    _check_diagnostics(got, O.diagnostics(prob, U))
+    unweighted = sum(d["mean_abs_v_last"] for d in parts) / 5
+    assert abs(unweighted - got["mean_abs_v_last"]) > 1e-6 * got["mean_abs_v_last"]
+    parts[3]["status"] = 4
+    assert combine_diagnostics(parts, [dec.cells(r) for r in range(5)])["status"] == 4

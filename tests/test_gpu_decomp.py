@@ -16,7 +16,7 @@ import pytest
 
 import oracle as O
 from paper_1903_09043_gb300 import inputs as I
-from paper_1903_09043_gb300.decomp import DecomposedSolver, SlabDecomposition, advance_local
+from paper_1903_09043_gb300.decomp import DecomposedSolver, SlabDecomposition, advance_local, combine_diagnostics
 from parity import F32_STEP_TOL, F64_TOL, field_errors
 
 pytestmark = pytest.mark.gpu
@@ -59,11 +59,19 @@ def _run_slabs(prob, U, parts, precision, nsteps):
             s.set_state(V)
         dt = advance_local(dec, solvers, nsteps)
         out = dec.join([s.get_state() for s in solvers])
-        status = max(s.diagnostics(check=False)["status"] for s in solvers)
+        diag = combine_diagnostics([s.diagnostics(check=False) for s in solvers], [dec.cells(r) for r in range(parts)])
     finally:
         for s in solvers:
             s.close()
-    return out, dt, status
+    return out, dt, diag
+
+
+def _check_diagnostics(got, want, tol):
+    """Whole-grid diagnostics combined from the slabs against the oracle's
+    of the undivided grid (momenta relative to the mass scale)."""
+    for k, v in want.items():
+        scale = max(abs(v), abs(want["mass"]) if k.startswith("mom") else abs(v), 1e-300)
+        assert abs(got[k] - v) <= tol * scale, (k, got[k], v)
 
 
 @pytest.mark.parametrize("case", sorted(CASES))
@@ -72,8 +80,8 @@ def test_slabs_on_one_gpu_match_undivided_grid_and_oracle(case, precision):
     make, parts = CASES[case]
     prob, U = make()
     n = 12
-    V, dt, status = _run_slabs(prob, U, parts, precision, n)
-    assert status == 0
+    V, dt, diag = _run_slabs(prob, U, parts, precision, n)
+    assert diag["status"] == 0
     ref, t, dts = O.run(prob, U, n, return_dt=True)
     errs = field_errors(prob, V, ref)
     assert max(errs) <= (F64_TOL if precision == "f64" else n * F32_STEP_TOL), errs
@@ -86,6 +94,7 @@ def test_slabs_on_one_gpu_match_undivided_grid_and_oracle(case, precision):
             W = s.get_state()
         assert max(field_errors(prob, V, W)) <= 1e-14
         assert dt == pytest.approx(dts[-1], rel=1e-14)
+        _check_diagnostics(diag, O.diagnostics(prob, ref), 1e-12)
 
 
 def test_halo_calls_reject_a_side_without_halo():
@@ -120,8 +129,9 @@ def _worker(rank, world, port, nsteps, q):
         dec = SlabDecomposition(prob, world)
         with ark.Solver(dec.sub_problem(rank), "f64") as s:
             s.set_state(dec.split(U)[rank])
-            dt = DecomposedSolver(dec, rank, s).step(nsteps)
-            q.put((rank, s.get_state(), dt))
+            ds = DecomposedSolver(dec, rank, s)
+            dt = ds.step(nsteps)
+            q.put((rank, s.get_state(), dt, ds.global_diagnostics()))
     finally:
         dist.destroy_process_group()
 
@@ -136,7 +146,7 @@ def test_two_gloo_ranks_sharing_the_gpu():
     procs = [ctx.Process(target=_worker, args=(r, 2, port, 10, q)) for r in range(2)]
     for p in procs:
         p.start()
-    got = dict((r, (V, dt)) for r, V, dt in (q.get(timeout=300) for _ in range(2)))
+    got = dict((r, (V, dt, dg)) for r, V, dt, dg in (q.get(timeout=300) for _ in range(2)))
     for p in procs:
         p.join(120)
         assert p.exitcode == 0
@@ -145,3 +155,5 @@ def test_two_gloo_ranks_sharing_the_gpu():
     ref, t, dts = O.run(prob, U, 10, return_dt=True)
     assert max(field_errors(prob, dec.join([got[0][0], got[1][0]]), ref)) <= F64_TOL
     assert got[0][1] == pytest.approx(dts[-1], rel=1e-14) and got[1][1] == got[0][1]
+    for r in range(2):
+        _check_diagnostics(got[r][2], O.diagnostics(prob, ref), 1e-12)
