@@ -7,9 +7,10 @@
 // two-cell in-plane halo, R2X x R2Y threads in all, and keeps that column's
 // whole vertical pipeline in registers -- conserved and face values of the
 // planes behind the front, tilde states, the upwind flux through the lower
-// face, the viscous z flux.  Shared memory only exchanges in-plane
-// neighbours: every exchange array is single-buffered at a fixed offset, so
-// each access is the thread's own slot plus a constant.
+// face, the viscous z flux.  Shared memory exchanges in-plane neighbours
+// (every exchange array single-buffered at a fixed offset, so each access is
+// the thread's own slot plus a constant) and, in 2D, stages each column's
+// next planes (Step2Cfg::RING); 3D prefetches the next plane into registers.
 //
 // The vertical pipeline is skewed so that one plane needs two barriers.  At
 // front plane f:
