@@ -9,8 +9,9 @@
 // planes behind the front, tilde states, the upwind flux through the lower
 // face, the viscous z flux.  Shared memory exchanges in-plane neighbours
 // (every exchange array single-buffered at a fixed offset, so each access is
-// the thread's own slot plus a constant) and, in 2D, stages each column's
-// next planes (Step2Cfg::RING); 3D prefetches the next plane into registers.
+// the thread's own slot plus a constant) and stages each column's next
+// planes (Step2Cfg::RING) where that measured faster than prefetching the next
+// plane into registers.
 //
 // The vertical pipeline is skewed so that one plane needs two barriers.  At
 // front plane f:
@@ -61,15 +62,16 @@ struct Step2Cfg {
     static constexpr int BRING = 8;                               // base rows kept in shared memory (split form)
     static constexpr size_t O_BASE = ((N_REAL * sizeof(Real) + 15) / 16) * 16;
     static constexpr size_t O_RED = O_BASE + (SPLIT ? BRING * BSTRIDE * sizeof(float) : 0);
-    // 2D: each thread copies its own column three planes ahead into a shared
-    // ring of 4 planes (cp.async), which hides the load latency of a 2D block's
-    // short planes (about 1 us each); in the split form the first BSTRIDE
-    // threads copy the base row each plane needs in the same group, so no
-    // thread waits on a load before a barrier.  The viscous split step of one
-    // grid (ENS false: not an ensemble item) keeps the one-plane register
-    // prefetch, which its longer planes hide and which measured faster there,
-    // as does 3D, where a plane takes ten times longer.
-    static constexpr bool RING = DIM == 2 && !PHIA && !(SPLIT && VISC && !ENS);
+    // Each thread copies its own column three planes ahead into a shared ring
+    // of 4 planes (cp.async); in the split form the first BSTRIDE threads copy
+    // the base row each plane needs in the same group, so no thread waits on a
+    // load before a barrier.  This hides the load latency of a 2D block's short
+    // planes (about 1 us each).  The viscous split step of one 2D grid (ENS
+    // false: not an ensemble item) keeps the one-plane register prefetch, which
+    // its longer planes hide and which measured faster there; in 3D, where a
+    // plane takes ten times longer, the ring pays only in the split form (whose
+    // base rows it also carries), and plain FP32 keeps the register prefetch.
+    static constexpr bool RING = !PHIA && (DIM == 3 ? SPLIT : !(SPLIT && VISC && !ENS));
     static constexpr size_t O_RING = O_RED + NT * sizeof(double) + 4 * sizeof(double);
     static constexpr size_t SMEM_BYTES = O_RING + (RING ? 4 * NF * NT * sizeof(Real) : 0);
     static_assert(NT % 32 == 0 && NT <= 1024, "block must be whole warps");
@@ -77,8 +79,8 @@ struct Step2Cfg {
 
 // Four consecutive base-table entries of one row.  The block keeps the rows
 // it is using in a shared ring of BRING rows (slot r & (BRING - 1)), filled
-// ahead of use (one plane ahead in 3D, with the state ring's copies in 2D), so
-// each read is a 16-byte shared broadcast.
+// ahead of use (with the state ring's copies, or one plane ahead without the
+// ring), so each read is a 16-byte shared broadcast.
 struct Base4 {
     float x, y, z, w;
 };
