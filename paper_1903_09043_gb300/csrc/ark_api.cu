@@ -388,8 +388,9 @@ ark_status ark_set_state(ark_handle* h, const double* U, int on_device)
     if (h->prec == ARK_F32_SPLIT) {
         const int nv = nv_of(h), L = nv + 4;
         double* means = nullptr;
-        cudaError_t e = cudaMallocAsync((void**)&means, 2 * (size_t)nv * sizeof(double), h->stream);
-        if (e == cudaSuccess) e = ark::launch_row_means(a, src, means, means + nv, h->stream);
+        cudaError_t e = cudaMallocAsync((void**)&means, (2 * (size_t)nv + ark::row_means_scratch(a)) * sizeof(double),
+                                        h->stream);
+        if (e == cudaSuccess) e = ark::launch_row_means(a, src, means + 2 * nv, means, means + nv, h->stream);
         std::vector<double> hm(2 * (size_t)nv);
         if (e == cudaSuccess) e = cudaMemcpyAsync(hm.data(), means, hm.size() * sizeof(double), cudaMemcpyDeviceToHost, h->stream);
         if (e == cudaSuccess) e = cudaStreamSynchronize(h->stream);

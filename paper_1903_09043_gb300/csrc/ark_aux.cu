@@ -137,19 +137,25 @@ __global__ void __launch_bounds__(AUX_THREADS) halo_set_kernel(const StepArgs a,
     }
 }
 
-// One block per row of the last axis; fixed-order tree sums.
-template <int D>
+// Horizontal means of rho and p, pass 1: block (r, c) sums chunk c of row r
+// (ROW_CHUNK cells; fixed-order tree sums) into part[r * chunks + c].  NA:
+// the covolume law divides p by 1 - b rho; the stiffened gas (b = 0) skips
+// that division, one of the two FP64 divisions per cell of this FP64-bound
+// pass.
+constexpr long long ROW_CHUNK = 8192;
+template <int D, bool NA>
 __global__ void __launch_bounds__(AUX_THREADS) row_means_kernel(const StepArgs a, const double* __restrict__ U,
-                                                                  double* rho_mean, double* p_mean)
+                                                                  double* part_r, double* part_p)
 {
     __shared__ double sr[AUX_THREADS], sp[AUX_THREADS];
-    const int r = blockIdx.x;
+    const int r = blockIdx.x, c = blockIdx.y, chunks = gridDim.y;   // rows in x: no 65535 limit
     const long long plane = D == 3 ? (long long)a.n[0] * a.n[1] : (long long)a.n[0];
     // a caller's potential (split form: separable, one value per row) from the
     // FP64 row table, else the uniform-gravity potential
     const double phi = a.phiA ? a.base64[3 * (a.n[D - 1] + 4) + r + 2] : -(a.g * (a.lo_v + (r + 0.5) * a.dx[D - 1]));
+    const long long i1 = min(plane, (c + 1) * ROW_CHUNK);
     double accr = 0.0, accp = 0.0;
-    for (long long i = threadIdx.x; i < plane; i += AUX_THREADS) {
+    for (long long i = c * ROW_CHUNK + threadIdx.x; i < i1; i += AUX_THREADS) {
         const long long idx = r * plane + i;
         const double rho = U[idx];
         double m2 = 0.0;
@@ -158,9 +164,10 @@ __global__ void __launch_bounds__(AUX_THREADS) row_means_kernel(const StepArgs a
             const double m = U[(1 + d) * a.ncell + idx];
             m2 += m * m;
         }
-        const double ke = 0.5 * m2 / rho;   // one FP64 division per cell
+        const double ke = 0.5 * m2 / rho;
         accr += rho;
-        accp += (a.gamma - 1.0) * (U[(D + 1) * a.ncell + idx] - ke - rho * phi) / (1.0 - a.b * rho) - a.dgpinf;
+        const double re = (a.gamma - 1.0) * (U[(D + 1) * a.ncell + idx] - ke - rho * phi);
+        accp += (NA ? re / (1.0 - a.b * rho) : re) - a.dgpinf;
     }
     sr[threadIdx.x] = accr;
     sp[threadIdx.x] = accp;
@@ -173,9 +180,24 @@ __global__ void __launch_bounds__(AUX_THREADS) row_means_kernel(const StepArgs a
         __syncthreads();
     }
     if (threadIdx.x == 0) {
-        rho_mean[r] = sr[0] / double(plane);
-        p_mean[r] = sp[0] / double(plane);
+        part_r[(long long)r * chunks + c] = sr[0];
+        part_p[(long long)r * chunks + c] = sp[0];
     }
+}
+
+// Pass 2: one thread per row sums its chunks in order.
+__global__ void row_means_final_kernel(const double* __restrict__ part_r, const double* __restrict__ part_p,
+                                       int chunks, int nv, double plane, double* rho_mean, double* p_mean)
+{
+    const int r = blockIdx.x * blockDim.x + threadIdx.x;
+    if (r >= nv) return;
+    double sr = 0.0, sp = 0.0;
+    for (int c = 0; c < chunks; ++c) {
+        sr += part_r[(long long)r * chunks + c];
+        sp += part_p[(long long)r * chunks + c];
+    }
+    rho_mean[r] = sr / plane;
+    p_mean[r] = sp / plane;
 }
 
 template <int D, typename Real, bool SPLIT>
@@ -351,11 +373,31 @@ cudaError_t launch_convert_out(const StepArgs& a, int prec, const void* Uin, dou
     return cudaGetLastError();
 }
 
-cudaError_t launch_row_means(const StepArgs& a, const double* U, double* rho_mean, double* p_mean, cudaStream_t s)
+static int row_chunks(const StepArgs& a)
 {
-    const int nv = a.n[a.dim - 1];
-    if (a.dim == 2) row_means_kernel<2><<<nv, AUX_THREADS, 0, s>>>(a, U, rho_mean, p_mean);
-    else row_means_kernel<3><<<nv, AUX_THREADS, 0, s>>>(a, U, rho_mean, p_mean);
+    const long long plane = a.dim == 3 ? (long long)a.n[0] * a.n[1] : (long long)a.n[0];
+    return (int)((plane + ROW_CHUNK - 1) / ROW_CHUNK);
+}
+
+size_t row_means_scratch(const StepArgs& a) { return 2 * (size_t)a.n[a.dim - 1] * (size_t)row_chunks(a); }
+
+cudaError_t launch_row_means(const StepArgs& a, const double* U, double* scratch, double* rho_mean, double* p_mean,
+                             cudaStream_t s)
+{
+    const int nv = a.n[a.dim - 1], chunks = row_chunks(a);
+    const long long plane = a.dim == 3 ? (long long)a.n[0] * a.n[1] : (long long)a.n[0];
+    double* part_r = scratch;
+    double* part_p = scratch + (size_t)nv * chunks;
+    const dim3 grid((unsigned)nv, (unsigned)chunks);
+    const bool na = a.b != 0.0;
+    if (a.dim == 2) {
+        if (na) row_means_kernel<2, true><<<grid, AUX_THREADS, 0, s>>>(a, U, part_r, part_p);
+        else row_means_kernel<2, false><<<grid, AUX_THREADS, 0, s>>>(a, U, part_r, part_p);
+    } else {
+        if (na) row_means_kernel<3, true><<<grid, AUX_THREADS, 0, s>>>(a, U, part_r, part_p);
+        else row_means_kernel<3, false><<<grid, AUX_THREADS, 0, s>>>(a, U, part_r, part_p);
+    }
+    row_means_final_kernel<<<(nv + 127) / 128, 128, 0, s>>>(part_r, part_p, chunks, nv, double(plane), rho_mean, p_mean);
     return cudaGetLastError();
 }
 

@@ -22,8 +22,12 @@ cudaError_t launch_convert_out(const StepArgs& a, int prec, const void* Uin, dou
 cudaError_t launch_halo_get(const StepArgs& a, int prec, int side, const void* U, double* out, cudaStream_t s);
 cudaError_t launch_halo_set(const StepArgs& a, int prec, const double* in, void* halo, cudaStream_t s);
 
-// Horizontal means of rho and p of an FP64 full state, one per row of the last axis.
-cudaError_t launch_row_means(const StepArgs& a, const double* U, double* rho_mean, double* p_mean, cudaStream_t s);
+// Horizontal means of rho and p of an FP64 full state, one per row of the last
+// axis: per-chunk partial sums into `scratch` (row_means_scratch(a) doubles),
+// then each row's chunks summed in order.
+size_t row_means_scratch(const StepArgs& a);
+cudaError_t launch_row_means(const StepArgs& a, const double* U, double* scratch, double* rho_mean, double* p_mean,
+                             cudaStream_t s);
 
 // Diagnostics: per-block FP64 partial sums in a fixed order, then one fixed-order reduction.
 enum { DG_MASS = 0, DG_MX, DG_MY, DG_MZ, DG_W, DG_KE, DG_VABS, DG_NSUM };
