@@ -737,6 +737,9 @@ NOBLE_ABEL_CASES = {
     "3d_strat_noslip_visc_multi_tile": lambda: I.stratified_random(3, (35, 33, 12), mu=0.005, kappa=0.01, b=0.25),
     "3d_strat_reflect": lambda: I.stratified_random(3, (19, 6, 8), walls=I.REFLECT_HYDRO, p_inf=0.3, b=0.2),
     "3d_periodic_visc": _na_periodic,
+    # planes of more than 8192 cells: the split form's base state sums each row in chunks
+    "3d_strat_two_chunk_rows": lambda: I.stratified_random(3, (96, 90, 6), mu=0.005, kappa=0.01, b=0.25),
+    "2d_strat_two_chunk_rows": lambda: I.stratified_random(2, (8300, 4), mu=0.01, kappa=0.02, p_inf=0.2, b=0.2),
 }
 
 
